@@ -1,0 +1,162 @@
+"""FP64 CPU oracle for COO MTTKRP, the sparse CP loss and its gradient.
+
+TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the ``cpu_baseline`` / ``--impl reference``
+legs of ``bench.py`` may import this package.  It shares no code with the CUDA
+library (``paper_1902_03317_gb300``) and never imports it.
+
+The arithmetic lives in ``pasta_oracle.c`` (plain C, FP64, single thread, built
+with ``gcc -O2 -fno-fast-math``); this module only builds that file, marshals
+numpy arrays into it, and adds the mode-order sort, which is a library stable
+sort (``numpy.lexsort``) used as one step.
+
+Citations are to arXiv:1902.03317 (PASTA):
+  - MTTKRP: Eq. (mttkrp-init) in Sec. 3.6 and Algorithm 6 (Sec. 5.2.6).
+  - COO layout and 0-based indices: Sec. 5.1.
+  - Row-major factors, element (i, r) at i*R + r: footnote in Sec. 3.4 and
+    Algorithm 6.
+  - Sorting "in the order of mode 1 > 2 > 3", lexicographic: Sec. 5.2.2
+    (Algorithm 2's preprocessing); mode orientation: Sec. 2.3.
+  - CP model and gradient-descent CPD: Sec. 2.2 (the loss itself is not
+    printed in the paper; it is the least-squares objective over the stored
+    entries).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pasta_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile ``pasta_oracle.c`` into ``oracle/_build/liboracle.so``."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-fno-fast-math", "-ffp-contract=off", "-std=c11",
+           "-shared", "-fPIC", "-o", tmp, _SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            for name, argt in {
+                "oracle_mttkrp": [ctypes.c_int, P, ctypes.c_uint64, P, P, P,
+                                  ctypes.c_int, ctypes.c_int, P],
+                "oracle_cp_loss": [ctypes.c_int, P, ctypes.c_uint64, P, P, P,
+                                   ctypes.c_int, P, P],
+                "oracle_cp_grad": [ctypes.c_int, P, ctypes.c_uint64, P, P, P,
+                                   ctypes.c_int, ctypes.c_double, P],
+            }.items():
+                fn = getattr(lib, name)
+                fn.argtypes = argt
+                fn.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def _prep(dims, idx, val, U, R):
+    dims = np.ascontiguousarray(np.asarray(dims, dtype=np.uint64))
+    order = int(dims.shape[0])
+    idx = [np.ascontiguousarray(np.asarray(ix).astype(np.uint32, copy=False)) for ix in idx]
+    if len(idx) != order:
+        raise ValueError("need one index array per mode")
+    nnz = int(idx[0].shape[0]) if order else 0
+    for ix in idx:
+        if ix.shape != (nnz,):
+            raise ValueError("index arrays must all have length nnz")
+    val = np.ascontiguousarray(np.asarray(val, dtype=np.float64))
+    if val.shape != (nnz,):
+        raise ValueError("val must have length nnz")
+    Ud = []
+    for k in range(order):
+        if U[k] is None:
+            Ud.append(np.zeros((int(dims[k]), R)))
+        else:
+            u = np.ascontiguousarray(np.asarray(U[k], dtype=np.float64))
+            if u.shape != (int(dims[k]), R):
+                raise ValueError(f"U[{k}] must be {int(dims[k])} x {R}")
+            Ud.append(u)
+    idx_ptrs = (ctypes.c_void_p * order)(*[_ptr(ix) for ix in idx])
+    u_ptrs = (ctypes.c_void_p * order)(*[_ptr(u) for u in Ud])
+    return dims, order, nnz, idx, val, Ud, idx_ptrs, u_ptrs
+
+
+def mttkrp(dims, idx, val, U, mode: int, R: int | None = None) -> np.ndarray:
+    """Mode-``mode`` MTTKRP in FP64: Eq. (mttkrp-init), element-wise as in
+    Algorithm 6.  ``U[mode]`` may be ``None``.  Returns ``dims[mode] x R``."""
+    if R is None:
+        R = next(np.asarray(u).shape[1] for k, u in enumerate(U) if u is not None and k != mode)
+    dims, order, nnz, idx, val, Ud, ip, up = _prep(dims, idx, val, U, R)
+    M = np.empty((int(dims[mode]), R), dtype=np.float64)
+    rc = _load().oracle_mttkrp(order, _ptr(dims), nnz, ip, _ptr(val), up,
+                               int(mode), int(R), _ptr(M))
+    if rc != 0:
+        raise ValueError("oracle_mttkrp rejected its arguments")
+    return M
+
+
+def cp_loss(dims, idx, val, U, want_resid: bool = False):
+    """Sparse CP least-squares loss 1/2 sum_m (x_m - sum_r prod_k U_k(i_k,r))^2
+    in FP64.  Returns ``loss`` or ``(loss, resid)``."""
+    R = int(np.asarray(U[0]).shape[1])
+    dims, order, nnz, idx, val, Ud, ip, up = _prep(dims, idx, val, U, R)
+    loss = np.zeros(1, dtype=np.float64)
+    resid = np.empty(nnz, dtype=np.float64) if want_resid else None
+    rc = _load().oracle_cp_loss(order, _ptr(dims), nnz, ip, _ptr(val), up, R,
+                                _ptr(resid) if want_resid else None, _ptr(loss))
+    if rc != 0:
+        raise ValueError("oracle_cp_loss rejected its arguments")
+    return (float(loss[0]), resid) if want_resid else float(loss[0])
+
+
+def cp_grad(dims, idx, val, U, g: float = 1.0):
+    """Gradient of ``g * cp_loss`` with respect to every factor, FP64.
+    Returns a list of ``dims[k] x R`` arrays."""
+    R = int(np.asarray(U[0]).shape[1])
+    dims, order, nnz, idx, val, Ud, ip, up = _prep(dims, idx, val, U, R)
+    G = [np.empty((int(dims[k]), R), dtype=np.float64) for k in range(order)]
+    gp = (ctypes.c_void_p * order)(*[_ptr(x) for x in G])
+    rc = _load().oracle_cp_grad(order, _ptr(dims), nnz, ip, _ptr(val), up, R,
+                                float(g), gp)
+    if rc != 0:
+        raise ValueError("oracle_cp_grad rejected its arguments")
+    return G
+
+
+def mode_order(order: int, mode: int) -> list[int]:
+    """Cyclic mode order starting at ``mode``: (n, n+1, ..., N-1, 0, ..., n-1).
+    Sec. 5.2.2 sorts "in the order of mode 1 > 2 > 3"; for a mode-n sort the
+    output mode leads and the rest follow cyclically."""
+    return [(mode + j) % order for j in range(order)]
+
+
+def sort_perm(idx, mode: int) -> np.ndarray:
+    """Stable lexicographic sort of the stored entries in cyclic mode order
+    from ``mode`` (``numpy.lexsort`` as a library step).  Returns the
+    permutation p with sorted position q holding original entry p[q]; equal
+    coordinates keep their storage order."""
+    order = len(idx)
+    keys = [np.asarray(idx[k]).astype(np.int64) for k in reversed(mode_order(order, mode))]
+    return np.lexsort(keys).astype(np.int64)
