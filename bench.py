@@ -1,0 +1,430 @@
+"""Benchmark: COO MTTKRP throughput (nnz/s, fraction of the HBM roofline) and
+CP-loss forward+backward time, FP32 vs BF16 factors, on one GB300 per rank.
+
+Workload (default, the measured shape): zipf3d, a 1M x 500k x 200k COO tensor
+with 100M distinct coordinates, each mode's index Zipf(s=1.1), lognormal(0,1)
+values, R = 32 FP32 factors (synthetic, seeded; stands in for the paper's
+FROSTT-style tensors).
+
+One timed step = one pass of the hot path over the tensor: MTTKRP on every
+mode (each on its mode-sorted copy) followed by the CP-loss forward and
+backward (all modes in one pass).  The mode sorts are preprocessing: they run
+once before timing, as the paper's "provided" sort does, and their time is
+reported under "preprocess".  `value` = N modes x nnz / (MTTKRP part of the
+step), summed over ranks, with device time taken by CUDA events on the
+launching stream and the maximum over ranks.  The COO stream (1.6 GB) is
+larger than L2, so no L2 flush is inserted.
+
+`--impl reference` times the FP64 CPU oracle on the host cores (a bounded
+sample of the same workload); the reference paper has no GPU code.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MTTKRP nnz/s & % of HBM roofline; CP-loss fwd+bwd time BF16 vs FP32"
+DEFAULT_WORKLOAD = "zipf3d"
+LOSS_WORKLOAD = "cploss3d"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-loss-compare", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=12_000_000,
+                    help="entries of the workload the CPU oracle runs on")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_desc(wl) -> str:
+    dims = " x ".join(f"{d:,}" for d in wl.dims)
+    what = "distinct" if wl.distinct else "with duplicates"
+    dist = "/".join(sorted(set(wl.index_dist)))
+    return (f"{wl.name}: {dims}, nnz={wl.nnz:,} {what}, indices {dist}"
+            f"{f' s={wl.zipf_s}' if 'zipf' in wl.index_dist else ''}, values {wl.values}, R={wl.R}")
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            import tempfile
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        sm_sorted = sorted(sm)
+        return {"sm_mhz": sm_sorted[len(sm_sorted) // 2] if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------- roofline inputs --
+
+def measured_peak_gbs():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("mttkrp.cu", "pasta_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_1902_03317_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload: str):
+    """DRAM bytes per MTTKRP launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"k_mttkrp_{workload}_traffic.txt")
+    try:
+        kv = {}
+        for line in open(p):
+            if ":" in line and not line.startswith("#"):
+                k, v = line.split(":", 1)
+                kv[k.strip()] = v.strip()
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+            return None
+        return float(kv["dram_bytes_per_launch_full_size"])
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------ own (GPU) --
+
+def run_own(args, rank, world, local):
+    import torch
+    import torch.distributed as dist
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1902_03317_gb300 as pasta
+    from paper_1902_03317_gb300 import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1 and not dist.is_initialized():
+        dist.init_process_group("gloo")
+
+    wl = synth.WORKLOADS[args.workload]
+    N = wl.order
+    # ---- inputs, resident in HBM
+    Xd = synth.generate(wl, device=dev)
+    Us = synth.factors_for(wl, device=dev)
+    X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
+    # rows of each factor touched (algorithmic bytes), counted before timing
+    touched = [int(torch.unique(ix).numel()) for ix in Xd.idx]
+    t_sort = []
+    for n in range(N):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        X.sort_by_mode(n)
+        torch.cuda.synchronize()
+        t_sort.append((time.perf_counter() - t0) * 1e3)
+    X.sort_by_mode(0)
+    Ms = [torch.empty((wl.dims[n], wl.R), device=dev) for n in range(N)]
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        for n in range(N):
+            if ev is not None:
+                ev[2 * n].record(stream)
+            pasta.mttkrp(X, Us, n, out=Ms[n])
+            if ev is not None:
+                ev[2 * n + 1].record(stream)
+        pasta.cp_loss_fwd(X, Us, 0)
+        pasta.cp_loss_bwd(X, Us, 0)
+        if ev is not None:
+            ev[2 * N].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * N + 1)] for _ in range(args.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    start.record(stream)
+    for k in range(args.steps):
+        step(evs[k])
+    end.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    total_ms = start.elapsed_time(end)
+    mttkrp_ms = [[evs[k][2 * n].elapsed_time(evs[k][2 * n + 1]) for n in range(N)] for k in range(args.steps)]
+    loss_ms = [evs[k][2 * N - 1].elapsed_time(evs[k][2 * N]) for k in range(args.steps)]
+    sweep_ms = sum(sum(r) for r in mttkrp_ms) / args.steps
+    per_mode_ms = [sum(mttkrp_ms[k][n] for k in range(args.steps)) / args.steps for n in range(N)]
+    loss_ms_mean = sum(loss_ms) / args.steps
+    step_ms = total_ms / args.steps
+    if world > 1:
+        t = torch.tensor([sweep_ms, step_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        sweep_ms, step_ms = float(t[0]), float(t[1])
+
+    nnz = wl.nnz
+    value = world * N * nnz / (sweep_ms * 1e-3)
+    # algorithmic bytes per launch (mode n): COO stream (N 32-bit indices + FP32
+    # value per entry) + touched rows of the other factors + the output write
+    es = 4
+    alg_bytes = [nnz * (4 * N + 4) + sum(touched[k] * wl.R * es for k in range(N) if k != n)
+                 + wl.dims[n] * wl.R * 4 for n in range(N)]
+    achieved = sum(alg_bytes) / (sweep_ms * 1e-3) / 1e9
+    peak, peak_src = measured_peak_gbs()
+    traffic = profiled_traffic(args.workload)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "kernel": "k_mttkrp", "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
+                "alg_bytes_per_launch": alg_bytes,
+                "frac_vs_8TBs": round(achieved / 8000.0, 4)}
+
+    result = {
+        "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_desc(wl), "step": "MTTKRP every mode + CP-loss fwd + bwd (mode-0 copy)",
+                   "l2": "no flush: inputs larger than L2 (COO stream 1.6 GB)",
+                   "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "breakdown_ms": {"mttkrp_per_mode": [round(x, 4) for x in per_mode_ms],
+                         "loss_fwd_bwd": round(loss_ms_mean, 4)},
+        "preprocess": {"sort_ms_per_mode": [round(x, 2) for x in t_sort]},
+        "gpu_launches": args.steps * (N + 2 + 1),
+        "clocks": clk,
+    }
+    del Xd
+    torch.cuda.empty_cache()
+
+    if not args.no_loss_compare and rank == 0:
+        result["cp_loss"] = loss_compare(pasta, synth, dev, args)
+    if not args.no_e2e:
+        result["e2e"] = e2e(pasta, synth, wl, dev, args, world)
+    if rank == 0 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(wl, args)
+    X.close()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def loss_compare(pasta, synth, dev, args):
+    """CP-loss forward+backward time, FP32 vs BF16 factors (cploss3d)."""
+    import torch
+    wl = synth.WORKLOADS[LOSS_WORKLOAD]
+    Xd = synth.generate(wl, device=dev)
+    X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
+    X.sort_by_mode(0)
+    del Xd
+    out = {"workload": workload_desc(wl)}
+    stream = torch.cuda.current_stream()
+    for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+        Us = [u.requires_grad_(True) for u in synth.factors_for(wl, device=dev, dtype=dt)]
+        for _ in range(3):
+            pasta.cp_loss(X, Us, 0).backward()
+        reps = max(5, args.steps)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        for _ in range(reps):
+            for u in Us:
+                u.grad = None
+            pasta.cp_loss(X, Us, 0).backward()
+        b.record(stream)
+        torch.cuda.synchronize()
+        out[f"{name}_fwd_bwd_ms"] = round(a.elapsed_time(b) / reps, 4)
+    out["bf16_speedup"] = round(out["fp32_fwd_bwd_ms"] / out["bf16_fwd_bwd_ms"], 3)
+    X.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def e2e(pasta, synth, wl, dev, args, world):
+    """Same metric through the public API from pinned host buffers: every step
+    copies the COO tensor and factors in, builds the handle and sorted
+    copies, runs the MTTKRP sweep and reads every output back."""
+    import torch
+    Xh = synth.generate(wl, device=dev)
+    idx_h = [i.cpu().pin_memory() for i in Xh.idx]
+    val_h = Xh.val.cpu().pin_memory()
+    Uh = [u.cpu().pin_memory() for u in synth.factors_for(wl, device=dev)]
+    del Xh
+    torch.cuda.empty_cache()
+    N = wl.order
+    outs = [torch.empty((wl.dims[n], wl.R), dtype=torch.float32).pin_memory() for n in range(N)]
+    h2d = sum(t.numel() * t.element_size() for t in idx_h + [val_h] + Uh)
+    d2h = sum(t.numel() * t.element_size() for t in outs)
+
+    def one():
+        idx = [t.to(dev, non_blocking=True) for t in idx_h]
+        val = val_h.to(dev, non_blocking=True)
+        Us = [u.to(dev, non_blocking=True) for u in Uh]
+        X = pasta.CooTensor(wl.dims, idx, val, validate=False)
+        del idx, val
+        for n in range(N):
+            M = pasta.mttkrp(X, Us, n)
+            outs[n].copy_(M, non_blocking=True)
+        torch.cuda.synchronize()
+        X.close()
+
+    one()
+    steps = max(2, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        one()
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([dt], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dt = float(t[0])
+    torch.cuda.empty_cache()
+    return {"value": world * N * wl.nnz / dt, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": steps,
+            "includes": "H2D of COO+factors, create, sort every mode, MTTKRP every mode, D2H of outputs"}
+
+
+# ----------------------------------------------------------- CPU oracle --
+
+def oracle_sample(wl, sample: int):
+    """A bounded, seeded sample of the workload for the CPU oracle: the first
+    `sample` entries of the generated tensor (its storage order is random)."""
+    import numpy as np
+    import torch
+    from paper_1902_03317_gb300 import synth
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    Xd = synth.generate(wl, device=dev)
+    n = min(sample, wl.nnz)
+    idx = [i[:n].cpu().numpy().astype(np.uint32) for i in Xd.idx]
+    val = Xd.val[:n].cpu().numpy().astype(np.float64)
+    del Xd
+    U = [u.double().numpy() for u in synth.factors_for(wl)]
+    return idx, val, U, n
+
+
+def cpu_baseline(wl, args):
+    import oracle
+    idx, val, U, n = oracle_sample(wl, args.cpu_sample)
+    t0 = time.perf_counter()
+    for mode in range(wl.order):
+        oracle.mttkrp(wl.dims, idx, val, U, mode, wl.R)
+    dt = time.perf_counter() - t0
+    return {"value": wl.order * n / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {n:,} of {wl.nnz:,} entries (random storage order), MTTKRP on all "
+                      f"{wl.order} modes, FP64 C oracle, 1 thread: {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_1902_03317_gb300 import synth
+    import oracle
+    oracle.build()
+    wl = synth.WORKLOADS[args.workload]
+    sample = max(100_000, args.cpu_sample // max(1, args.steps))
+    idx, val, U, n = oracle_sample(wl, sample)
+    for _ in range(args.warmup):
+        oracle.mttkrp(wl.dims, idx, val, U, 0, wl.R)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for mode in range(wl.order):
+            oracle.mttkrp(wl.dims, idx, val, U, mode, wl.R)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = wl.order * n / dt
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_desc(wl), "step": f"oracle MTTKRP on all modes over {n:,} sampled entries"},
+        "cpu_baseline": {"value": value, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+                         "sample": f"first {n:,} of {wl.nnz:,} entries per step"},
+        "e2e": {"value": value, "unit": "nnz/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    run_own(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

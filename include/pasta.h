@@ -1,0 +1,210 @@
+/*
+ * pasta.h -- C ABI of libpasta: COO MTTKRP and the sparse CP least-squares
+ * loss on one NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow arXiv:1902.03317 (PASTA, a sparse tensor benchmark
+ * suite):
+ *   - COO storage, Sec. 5.1: per stored entry one index per mode ("inds") and
+ *     one value ("val"); 32-bit indices and FP32 values (Table 2 caption);
+ *     indices are 0-based (the Sec. 5.1 example names entries (1,0,0) and
+ *     (1,0,2)).
+ *   - MTTKRP, Eq. (mttkrp-init) in Sec. 3.6 and Algorithm 6 in Sec. 5.2.6.
+ *   - Sorting in mode order, Sec. 5.2.2 (Algorithm 2's preprocessing) and the
+ *     mode-orientation discussion of Sec. 2.3.
+ *   - Factor matrices U_k are I_k x R, stored row-major (element (i, r) at
+ *     i*R + r): the footnote to Eq. (ttm) in Sec. 3.4 transposes Kolda's
+ *     convention for row-major C storage, and Algorithm 6 indexes A(i*R + r).
+ *   - The CP model (a sum of R rank-one terms, Sec. 2.2) fitted by gradient
+ *     descent (Sec. 2.2 lists gradient-descent CPD); the loss is the
+ *     least-squares objective over the stored entries.
+ *
+ * General rules
+ *   - Every call returns a pasta_status.  Nothing aborts, throws or traps; a
+ *     CUDA runtime failure becomes PASTA_ERR_CUDA and its text is available
+ *     from pasta_last_error() on the same host thread.
+ *   - "d_" pointers are device pointers (cudaMalloc'ed or equivalent) on the
+ *     current CUDA device; "h_"/unprefixed pointers are host pointers.
+ *   - stream is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Compute calls enqueue work on it and return without synchronising;
+ *     results are ready when the stream reaches that point.
+ *   - Modes are 0-based: mode 0 is the paper's mode 1.
+ *   - Limits: 2 <= order <= PASTA_MAX_ORDER, 1 <= R <= PASTA_MAX_RANK,
+ *     nnz < 2^32 - 2^16, every dims[k] in [1, 2^32).
+ *   - Factor element type is one pasta_dtype for all modes of a call.  FP32,
+ *     BF16 and FP16 factors accumulate in FP32 and produce FP32 outputs; FP64
+ *     factors accumulate in FP64 and produce FP64 outputs.
+ *   - Fast path: R * sizeof(element) a multiple of 16 bytes and every factor
+ *     and output pointer 16-byte aligned (row loads and vector atomics are
+ *     16 bytes wide).  Otherwise a scalar path with the same results runs.
+ */
+#ifndef PASTA_H
+#define PASTA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PASTA_MAX_ORDER 8
+#define PASTA_MAX_RANK 256
+#define PASTA_VERSION 1
+
+typedef struct pasta_coo_s *pasta_coo; /* opaque, owned by the library */
+
+typedef enum {
+    PASTA_OK = 0,
+    PASTA_ERR_INVALID_ARG = 1,  /* a NULL/out-of-range argument or size */
+    PASTA_ERR_ALIGNMENT = 2,    /* reserved; misaligned data takes the scalar path */
+    PASTA_ERR_INDEX_OOB = 3,    /* an index >= dims[k] found at create time */
+    PASTA_ERR_NONFINITE = 4,    /* a NaN/Inf value found at create time */
+    PASTA_ERR_NOT_SORTED = 5,   /* the mode-sorted copy a call needs is missing */
+    PASTA_ERR_NOMEM = 6,        /* device allocation failed */
+    PASTA_ERR_CUDA = 7,         /* a CUDA runtime call failed (see pasta_last_error) */
+    PASTA_ERR_UNSUPPORTED = 8   /* a combination this build does not implement */
+} pasta_status;
+
+typedef enum {
+    PASTA_F32 = 0,
+    PASTA_BF16 = 1,
+    PASTA_F16 = 2,
+    PASTA_F64 = 3
+} pasta_dtype;
+
+/* Flags for pasta_coo_create. */
+#define PASTA_CREATE_DEFAULT 0u
+/* Skip the bounds / finiteness scan (and its one host synchronisation). The
+ * caller vouches that every index is < dims[k]; an out-of-range index is then
+ * undefined behaviour of the compute calls. */
+#define PASTA_CREATE_NO_VALIDATE 1u
+
+/* Short constant text for a status code. */
+const char *pasta_status_str(pasta_status s);
+
+/* Detail of the last failing call on this host thread ("" if none). */
+const char *pasta_last_error(void);
+
+/* PASTA_VERSION of the loaded library. */
+int pasta_version(void);
+
+/*
+ * pasta_coo_create -- copy a COO tensor (Sec. 5.1) into library-owned device
+ * memory.
+ *   out    receives the handle (set to NULL on failure)
+ *   order  number of modes N
+ *   dims   host array of N mode sizes
+ *   nnz    number of stored entries (0 allowed)
+ *   d_idx  host array of N device pointers; d_idx[k][m] is entry m's index in
+ *          mode k (uint32, nnz elements each; any alignment)
+ *   d_val  device pointer to nnz FP32 values
+ *   flags  PASTA_CREATE_DEFAULT or PASTA_CREATE_NO_VALIDATE
+ * The input arrays are only read, and may be freed once the stream has
+ * passed this call.  Storage order is kept ("creation order").  Unless
+ * PASTA_CREATE_NO_VALIDATE is given, a device scan counts out-of-range indices
+ * and non-finite values and this call waits for it: PASTA_ERR_INDEX_OOB /
+ * PASTA_ERR_NONFINITE are returned and no handle is made.  Duplicated
+ * coordinates are legal and stay separate entries.
+ */
+pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,
+                              const uint32_t *const *d_idx, const float *d_val,
+                              unsigned flags, void *stream);
+
+/* Free the handle and every copy it owns (synchronises the device). NULL is a no-op. */
+pasta_status pasta_coo_destroy(pasta_coo X);
+
+/* Order, dims (host array of >= order entries, may be NULL) and nnz of X. */
+pasta_status pasta_coo_info(pasta_coo X, int *order, uint64_t *dims, uint64_t *nnz);
+
+/*
+ * pasta_coo_sort_by_mode -- build (once) the copy of X sorted for mode
+ * `mode` (Sec. 5.2.2 sorts lexicographically in mode order; Sec. 2.3 notes
+ * that each iteration order wants its own copy).  The key is the coordinate
+ * in cyclic mode order (mode, mode+1, ..., N-1, 0, ..., mode-1), each mode
+ * taking ceil(log2(dims[k])) bits, truncated to its leading 64 bits; the sort
+ * is stable, so entries with equal keys keep creation order.  The copy holds
+ * sorted indices, values and the permutation perm (sorted position p holds
+ * creation-order entry perm[p]).  A second call for the same mode is a no-op.
+ * Temporary device memory (about 24 bytes per entry) is allocated and freed
+ * on the stream.
+ */
+pasta_status pasta_coo_sort_by_mode(pasta_coo X, int mode, void *stream);
+
+/*
+ * Read-only device views of one stored copy: mode in [0, N) is the
+ * mode-sorted copy (PASTA_ERR_NOT_SORTED if absent), mode == -1 the creation
+ * order copy (perm is then NULL).  d_idx receives N pointers.  The pointers
+ * stay valid until pasta_coo_destroy.  Any output pointer may be NULL.
+ */
+pasta_status pasta_coo_view(pasta_coo X, int mode, const uint32_t **d_idx,
+                            const float **d_val, const uint32_t **d_perm);
+
+/*
+ * Copy one stored copy (mode as for pasta_coo_view) into caller-owned device
+ * buffers of nnz elements each: d_idx_out (host array of N device pointers,
+ * uint32), d_val_out (FP32) and d_perm_out (uint32; must be NULL for mode -1).
+ * Any output may be NULL to skip it.  Asynchronous on `stream`.
+ */
+pasta_status pasta_coo_copy_out(pasta_coo X, int mode, uint32_t *const *d_idx_out,
+                                float *d_val_out, uint32_t *d_perm_out, void *stream);
+
+/*
+ * pasta_mttkrp -- mode-n MTTKRP, Eq. (mttkrp-init) / Algorithm 6:
+ *     M(i, r) = sum_{m : i_n(m) = i} val(m) * prod_{k != n} U_k(i_k(m), r).
+ *   d_U     host array of N device pointers to row-major dims[k] x R factors
+ *           of element type u_dtype; d_U[mode] is not read (may be NULL)
+ *   mode    output mode n; the mode-n sorted copy must exist
+ *           (pasta_coo_sort_by_mode), else PASTA_ERR_NOT_SORTED
+ *   d_M     device output, dims[mode] x R row-major, FP32 (FP64 when u_dtype
+ *           is PASTA_F64); overwritten (zero-filled, then accumulated, as the
+ *           paper's Algorithm 6 expects an initialised output)
+ * Rows of M that no entry reaches are 0.  Summation order differs from the
+ * sequential loop, so FP32 results match it to rounding, not bitwise.
+ */
+pasta_status pasta_mttkrp(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int mode,
+                          int R, void *d_M, void *stream);
+
+/*
+ * pasta_cp_loss_fwd -- sparse CP least-squares loss over the stored entries:
+ *     model(m) = sum_r prod_k U_k(i_k(m), r),   e(m) = val(m) - model(m),
+ *     loss = 1/2 * sum_m e(m)^2.
+ *   mode     which stored copy to stream: -1 = creation order, or a sorted
+ *            mode (PASTA_ERR_NOT_SORTED if absent)
+ *   d_loss   device FP64 scalar, overwritten; the sum is taken in FP64 in a
+ *            fixed order (the same inputs and launch give the same bits)
+ *   d_resid  optional device output of nnz residuals e(m) (FP32; FP64 when
+ *            u_dtype is PASTA_F64), in the order of the streamed copy
+ * Per-entry arithmetic is FP32 (FP64 for PASTA_F64 factors).
+ */
+pasta_status pasta_cp_loss_fwd(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int R,
+                               int mode, double *d_loss, void *d_resid, void *stream);
+
+/*
+ * pasta_cp_loss_bwd -- gradient of g * loss with respect to every factor, in
+ * one pass over the stored entries:
+ *     G_k(i, r) = -g * sum_{m : i_k(m) = i} e(m) * prod_{j != k} U_j(i_j(m), r)
+ * (-g times the mode-k MTTKRP of the residual tensor).  e(m) is recomputed
+ * from the factors.
+ *   mode     copy to stream, as for pasta_cp_loss_fwd; the sorted mode's
+ *            gradient is reduced in registers along runs of equal index, the
+ *            other modes' with vector atomics
+ *   d_gscale device FP64 scalar g (NULL means g = 1)
+ *   d_G      host array of N device pointers to dims[k] x R row-major outputs,
+ *            FP32 (FP64 for PASTA_F64 factors); all overwritten
+ */
+pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int R,
+                               int mode, const double *d_gscale, void *const *d_G, void *stream);
+
+/*
+ * pasta_convert -- element-wise conversion of n values between pasta_dtypes
+ * (round to nearest even on narrowing), e.g. FP32 gradient accumulators to
+ * BF16 parameters.  Not a paper operation; it keeps the mixed-precision
+ * backward on the device.
+ */
+pasta_status pasta_convert(const void *d_src, pasta_dtype src_dtype, void *d_dst,
+                           pasta_dtype dst_dtype, uint64_t n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PASTA_H */

@@ -1,0 +1,249 @@
+"""Python API over libpasta: COO handles, MTTKRP, CP loss and its autograd.
+
+PyTorch supplies device memory and the current CUDA stream; every step of the
+computation (copy-in and validation, mode sort, MTTKRP, loss forward and
+backward, gradient down-conversion) runs in libpasta's kernels.  Operations
+follow arXiv:1902.03317 (PASTA): COO storage (Sec. 5.1), mode-order sorting
+(Sec. 5.2.2), MTTKRP (Eq. (mttkrp-init), Algorithm 6) and the CP model behind
+gradient-descent CPD (Sec. 2.2).
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import torch
+
+from . import _lib
+
+_DTYPES = {
+    torch.float32: _lib.PASTA_F32,
+    torch.bfloat16: _lib.PASTA_BF16,
+    torch.float16: _lib.PASTA_F16,
+    torch.float64: _lib.PASTA_F64,
+}
+
+
+def pasta_dtype(dt: torch.dtype) -> int:
+    try:
+        return _DTYPES[dt]
+    except KeyError:
+        raise TypeError(f"unsupported factor dtype {dt}") from None
+
+
+def acc_dtype(dt: torch.dtype) -> torch.dtype:
+    """Output/accumulation dtype for factors of dtype ``dt``."""
+    return torch.float64 if dt == torch.float64 else torch.float32
+
+
+def _stream(device) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+class CooTensor:
+    """A COO tensor held by libpasta on one CUDA device (``pasta_coo``).
+
+    ``idx``: one int32/uint32-valued tensor of nnz indices per mode (0-based,
+    Sec. 5.1); ``val``: nnz FP32 values.  The data is copied into
+    library-owned, padded SoA arrays; the inputs may be freed afterwards.
+    """
+
+    def __init__(self, dims: Sequence[int], idx: Sequence[torch.Tensor], val: torch.Tensor,
+                 validate: bool = True):
+        dims = [int(d) for d in dims]
+        order = len(dims)
+        if len(idx) != order:
+            raise ValueError("need one index tensor per mode")
+        if not val.is_cuda:
+            raise ValueError("val must be a CUDA tensor")
+        self.device = val.device
+        self.dims = tuple(dims)
+        self.order = order
+        self.nnz = int(val.numel())
+        idx_c = []
+        for ix in idx:
+            if ix.device != self.device or ix.numel() != self.nnz:
+                raise ValueError("index tensors must be on val's device with nnz elements")
+            if ix.dtype not in (torch.int32, torch.uint32):
+                raise TypeError("indices must be int32 (values < 2^31) or uint32")
+            idx_c.append(ix.contiguous())
+        val_c = val.contiguous()
+        if val_c.dtype != torch.float32:
+            raise TypeError("values must be float32")
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = _lib.lib().pasta_coo_create(
+                ctypes.byref(h), order, _lib.u64_array(dims), self.nnz,
+                _lib.ptr_array([t.data_ptr() for t in idx_c]), val_c.data_ptr(),
+                _lib.PASTA_CREATE_DEFAULT if validate else _lib.PASTA_CREATE_NO_VALIDATE,
+                _stream(self.device))
+        _lib.check(st, "pasta_coo_create")
+        self._h = h
+        self._sorted: set[int] = set()
+
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        if self._h is None:
+            raise RuntimeError("CooTensor is closed")
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None:
+            _lib.lib().pasta_coo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sort_by_mode(self, mode: int) -> "CooTensor":
+        """Build the mode-``mode`` sorted copy (Sec. 5.2.2) if not present."""
+        if mode not in self._sorted:
+            with torch.cuda.device(self.device):
+                st = _lib.lib().pasta_coo_sort_by_mode(self.handle, int(mode), _stream(self.device))
+            _lib.check(st, "pasta_coo_sort_by_mode")
+            self._sorted.add(int(mode))
+        return self
+
+    def sort_all(self) -> "CooTensor":
+        for n in range(self.order):
+            self.sort_by_mode(n)
+        return self
+
+    def copy_out(self, mode: int = -1):
+        """Device copies of one stored copy: (idx list int32, val, perm or None)."""
+        idx = [torch.empty(self.nnz, dtype=torch.int32, device=self.device) for _ in range(self.order)]
+        val = torch.empty(self.nnz, dtype=torch.float32, device=self.device)
+        perm = None if mode < 0 else torch.empty(self.nnz, dtype=torch.int32, device=self.device)
+        with torch.cuda.device(self.device):
+            st = _lib.lib().pasta_coo_copy_out(
+                self.handle, int(mode), _lib.ptr_array([t.data_ptr() for t in idx]),
+                val.data_ptr(), perm.data_ptr() if perm is not None else None,
+                _stream(self.device))
+        _lib.check(st, "pasta_coo_copy_out")
+        return idx, val, perm
+
+
+def _factor_ptrs(X: CooTensor, Us: Sequence[torch.Tensor | None], skip: int = -1):
+    if len(Us) != X.order:
+        raise ValueError("need one factor per mode")
+    dt = None
+    R = None
+    ptrs = []
+    for k, U in enumerate(Us):
+        if U is None:
+            if k != skip:
+                raise ValueError(f"factor {k} is required")
+            ptrs.append(None)
+            continue
+        if U.device != X.device or U.dim() != 2 or U.shape[0] != X.dims[k]:
+            raise ValueError(f"factor {k} must be a {X.dims[k]} x R tensor on {X.device}")
+        if not U.is_contiguous():
+            raise ValueError(f"factor {k} must be contiguous (row-major)")
+        if dt is None:
+            dt, R = U.dtype, int(U.shape[1])
+        elif U.dtype != dt or int(U.shape[1]) != R:
+            raise ValueError("all factors must share dtype and R")
+        ptrs.append(U.data_ptr())
+    return _lib.ptr_array(ptrs), dt, R
+
+
+def mttkrp(X: CooTensor, Us: Sequence[torch.Tensor | None], mode: int,
+           out: torch.Tensor | None = None) -> torch.Tensor:
+    """Mode-``mode`` MTTKRP (Eq. (mttkrp-init)); ``Us[mode]`` may be None.
+    Sorts for ``mode`` first if needed.  Returns ``dims[mode] x R`` in FP32
+    (FP64 for FP64 factors)."""
+    X.sort_by_mode(mode)
+    ptrs, dt, R = _factor_ptrs(X, Us, skip=mode)
+    if out is None:
+        out = torch.empty((X.dims[mode], R), dtype=acc_dtype(dt), device=X.device)
+    elif out.shape != (X.dims[mode], R) or out.dtype != acc_dtype(dt) or not out.is_contiguous():
+        raise ValueError("bad out tensor")
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_mttkrp(X.handle, ptrs, pasta_dtype(dt), int(mode), R,
+                                     out.data_ptr(), _stream(X.device))
+    _lib.check(st, "pasta_mttkrp")
+    return out
+
+
+def cp_loss_fwd(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = -1,
+                want_resid: bool = False):
+    """Sparse CP least-squares loss over the stored entries (FP64 0-d tensor),
+    optionally with the residuals in the order of the streamed copy."""
+    if mode >= 0:
+        X.sort_by_mode(mode)
+    ptrs, dt, R = _factor_ptrs(X, Us)
+    loss = torch.empty((), dtype=torch.float64, device=X.device)
+    resid = torch.empty(X.nnz, dtype=acc_dtype(dt), device=X.device) if want_resid else None
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_cp_loss_fwd(X.handle, ptrs, pasta_dtype(dt), R, int(mode),
+                                          loss.data_ptr(),
+                                          resid.data_ptr() if resid is not None else None,
+                                          _stream(X.device))
+    _lib.check(st, "pasta_cp_loss_fwd")
+    return (loss, resid) if want_resid else loss
+
+
+def cp_loss_bwd(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = -1,
+                gscale: torch.Tensor | None = None) -> list[torch.Tensor]:
+    """Gradient of ``gscale * loss`` for every factor, in one pass; FP32
+    (FP64 for FP64 factors) accumulators."""
+    if mode >= 0:
+        X.sort_by_mode(mode)
+    ptrs, dt, R = _factor_ptrs(X, Us)
+    G = [torch.empty((d, R), dtype=acc_dtype(dt), device=X.device) for d in X.dims]
+    gp = None
+    if gscale is not None:
+        gscale = gscale.to(device=X.device, dtype=torch.float64).contiguous()
+        gp = gscale.data_ptr()
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_cp_loss_bwd(X.handle, ptrs, pasta_dtype(dt), R, int(mode), gp,
+                                          _lib.ptr_array([g.data_ptr() for g in G]),
+                                          _stream(X.device))
+    _lib.check(st, "pasta_cp_loss_bwd")
+    return G
+
+
+def convert(src: torch.Tensor, dtype: torch.dtype) -> torch.Tensor:
+    """Element-wise dtype conversion in libpasta (round to nearest even)."""
+    src = src.contiguous()
+    out = torch.empty(src.shape, dtype=dtype, device=src.device)
+    with torch.cuda.device(src.device):
+        st = _lib.lib().pasta_convert(src.data_ptr(), pasta_dtype(src.dtype), out.data_ptr(),
+                                      pasta_dtype(dtype), src.numel(), _stream(src.device))
+    _lib.check(st, "pasta_convert")
+    return out
+
+
+class CPLoss(torch.autograd.Function):
+    """loss = 1/2 sum_m (x_m - sum_r prod_k U_k(i_k(m), r))^2 over the stored
+    entries of X, with hand-written forward and backward kernels.
+
+    ``CPLoss.apply(X, mode, *Us)``: ``mode`` selects the stored copy streamed
+    (-1 = creation order; a sorted mode lets the backward reduce that mode's
+    gradient along runs).  Returns an FP64 0-d tensor; gradients come back in
+    each factor's dtype (FP32 accumulation, converted on the device)."""
+
+    @staticmethod
+    def forward(ctx, X: CooTensor, mode: int, *Us: torch.Tensor):
+        Us = [U.detach() for U in Us]
+        ctx.X = X
+        ctx.mode = mode
+        ctx.save_for_backward(*Us)
+        return cp_loss_fwd(X, Us, mode)
+
+    @staticmethod
+    def backward(ctx, grad_out: torch.Tensor):
+        Us = ctx.saved_tensors
+        G = cp_loss_bwd(ctx.X, Us, ctx.mode, gscale=grad_out.detach().reshape(()))
+        grads = []
+        for U, g in zip(Us, G):
+            grads.append(g if g.dtype == U.dtype else convert(g, U.dtype))
+        return (None, None, *grads)
+
+
+def cp_loss(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = -1) -> torch.Tensor:
+    """Differentiable sparse CP loss (see CPLoss)."""
+    return CPLoss.apply(X, mode, *Us)

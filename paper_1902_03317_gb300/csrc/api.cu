@@ -1,0 +1,432 @@
+// C ABI of libpasta (include/pasta.h): argument checking, ownership of the
+// stored copies, the bounds/finiteness scan, and dispatch to the kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "pasta_internal.cuh"
+
+namespace pasta {
+
+namespace {
+thread_local char g_err[512] = "";
+constexpr int kPartialsCap = 4096;
+}  // namespace
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+pasta_status cuda_fail(cudaError_t e, const char *where) {
+    set_error("%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? PASTA_ERR_NOMEM : PASTA_ERR_CUDA;
+}
+
+size_t dtype_size(pasta_dtype t) {
+    switch (t) {
+        case PASTA_F32: return 4;
+        case PASTA_BF16: return 2;
+        case PASTA_F16: return 2;
+        case PASTA_F64: return 8;
+    }
+    return 0;
+}
+
+Geometry make_geometry(int R, int vec, int elem_bytes) {
+    (void)elem_bytes;
+    Geometry g{};
+    g.vec = vec;
+    g.slots = (R + vec - 1) / vec;
+    int L = 1, sh = 0;
+    while (L < g.slots && L < 32) {
+        L <<= 1;
+        ++sh;
+    }
+    g.L = L;
+    g.lshift = sh;
+    g.J = (g.slots + L - 1) / L;
+    g.tile = std::max(4 * L, 512);
+    return g;
+}
+
+CooView view_of(const pasta_coo_s *X, const StoredCopy &c) {
+    CooView v{};
+    for (int k = 0; k < X->order; ++k) v.idx[k] = c.idx[k];
+    v.val = c.val;
+    v.nnz = X->nnz;
+    v.order = X->order;
+    return v;
+}
+
+namespace {
+
+bool ok_dtype(int t) { return t >= PASTA_F32 && t <= PASTA_F64; }
+
+pasta_status alloc_copy(pasta_coo_s *X, StoredCopy &c, bool with_perm) {
+    const size_t arr = (size_t)X->nnz_pad * 4;  // multiple of 4096 bytes
+    const int narr = X->order + 1 + (with_perm ? 1 : 0);
+    void *block = nullptr;
+    cudaError_t e = cudaMalloc(&block, arr * (size_t)narr);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes for a stored copy failed", arr * (size_t)narr);
+        return PASTA_ERR_NOMEM;
+    }
+    char *p = static_cast<char *>(block);
+    for (int k = 0; k < X->order; ++k, p += arr) c.idx[k] = reinterpret_cast<uint32_t *>(p);
+    c.val = reinterpret_cast<float *>(p);
+    p += arr;
+    c.perm = with_perm ? reinterpret_cast<uint32_t *>(p) : nullptr;
+    c.block = block;
+    return PASTA_OK;
+}
+
+void free_copy(StoredCopy &c) {
+    if (c.block) cudaFree(c.block);
+    c = StoredCopy{};
+}
+
+// counts[0]: indices >= dims[k] (any mode); counts[1]: non-finite values.
+__global__ void k_validate(CooView v, const uint64_t *dims_unused, unsigned long long *counts,
+                           uint64_t d0, uint64_t d1, uint64_t d2, uint64_t d3, uint64_t d4,
+                           uint64_t d5, uint64_t d6, uint64_t d7) {
+    const uint64_t dims[kMaxOrder] = {d0, d1, d2, d3, d4, d5, d6, d7};
+    unsigned long long bad_i = 0, bad_v = 0;
+    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.nnz;
+         m += (uint64_t)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int k = 0; k < kMaxOrder; ++k)
+            if (k < v.order && (uint64_t)v.idx[k][m] >= dims[k]) ++bad_i;
+        if (!isfinite(v.val[m])) ++bad_v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bad_i += __shfl_xor_sync(0xFFFFFFFFu, bad_i, o);
+        bad_v += __shfl_xor_sync(0xFFFFFFFFu, bad_v, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (bad_i) atomicAdd(&counts[0], bad_i);
+        if (bad_v) atomicAdd(&counts[1], bad_v);
+    }
+    (void)dims_unused;
+}
+
+}  // namespace
+
+pasta_status validate_coo(const pasta_coo_s *X, void *stream, uint64_t *bad_index,
+                          uint64_t *bad_value) {
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long *d_counts = nullptr;
+    PASTA_CUDA(cudaMallocAsync((void **)&d_counts, 2 * sizeof(unsigned long long), s));
+    unsigned long long h[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(d_counts, 0, sizeof(h), s);
+    if (e == cudaSuccess && X->nnz > 0) {
+        const CooView v = view_of(X, X->orig);
+        const int blocks = (int)std::min<uint64_t>((X->nnz + 255) / 256, (uint64_t)X->num_sms * 8);
+        const uint64_t *d = X->dims;
+        k_validate<<<blocks, 256, 0, s>>>(v, nullptr, d_counts, d[0], d[1], d[2], d[3], d[4], d[5],
+                                          d[6], d[7]);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h, d_counts, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(d_counts, s);
+    if (e != cudaSuccess) return cuda_fail(e, "validate_coo");
+    *bad_index = h[0];
+    *bad_value = h[1];
+    return PASTA_OK;
+}
+
+}  // namespace pasta
+
+using namespace pasta;
+
+extern "C" {
+
+const char *pasta_status_str(pasta_status s) {
+    switch (s) {
+        case PASTA_OK: return "PASTA_OK";
+        case PASTA_ERR_INVALID_ARG: return "PASTA_ERR_INVALID_ARG";
+        case PASTA_ERR_ALIGNMENT: return "PASTA_ERR_ALIGNMENT";
+        case PASTA_ERR_INDEX_OOB: return "PASTA_ERR_INDEX_OOB";
+        case PASTA_ERR_NONFINITE: return "PASTA_ERR_NONFINITE";
+        case PASTA_ERR_NOT_SORTED: return "PASTA_ERR_NOT_SORTED";
+        case PASTA_ERR_NOMEM: return "PASTA_ERR_NOMEM";
+        case PASTA_ERR_CUDA: return "PASTA_ERR_CUDA";
+        case PASTA_ERR_UNSUPPORTED: return "PASTA_ERR_UNSUPPORTED";
+    }
+    return "PASTA_ERR_UNKNOWN";
+}
+
+const char *pasta_last_error(void) { return g_err; }
+
+int pasta_version(void) { return PASTA_VERSION; }
+
+pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,
+                              const uint32_t *const *d_idx, const float *d_val, unsigned flags,
+                              void *stream) {
+    if (!out) {
+        set_error("out is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (order < 2 || order > PASTA_MAX_ORDER || !dims) {
+        set_error("order must be in [2, %d] and dims non-NULL", PASTA_MAX_ORDER);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < order; ++k) {
+        if (dims[k] < 1 || dims[k] > 0xFFFFFFFFull) {
+            set_error("dims[%d] = %llu out of [1, 2^32)", k, (unsigned long long)dims[k]);
+            return PASTA_ERR_INVALID_ARG;
+        }
+    }
+    if (nnz >= 0xFFFF0000ull) {
+        set_error("nnz must be < 2^32 - 2^16");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (flags & ~PASTA_CREATE_NO_VALIDATE) {
+        set_error("unknown flags 0x%x", flags);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (nnz > 0) {
+        if (!d_idx || !d_val) {
+            set_error("d_idx/d_val is NULL");
+            return PASTA_ERR_INVALID_ARG;
+        }
+        for (int k = 0; k < order; ++k)
+            if (!d_idx[k]) {
+                set_error("d_idx[%d] is NULL", k);
+                return PASTA_ERR_INVALID_ARG;
+            }
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    pasta_coo_s *X = new (std::nothrow) pasta_coo_s();
+    if (!X) return PASTA_ERR_NOMEM;
+    X->order = order;
+    for (int k = 0; k < order; ++k) X->dims[k] = dims[k];
+    X->nnz = nnz;
+    X->nnz_pad = std::max<uint64_t>(kPadEntries, (nnz + kPadEntries - 1) / kPadEntries * kPadEntries);
+    pasta_status st = PASTA_OK;
+    cudaError_t e = cudaGetDevice(&X->device);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&X->num_sms, cudaDevAttrMultiProcessorCount, X->device);
+    if (e != cudaSuccess) st = cuda_fail(e, "device query");
+    if (st == PASTA_OK) st = alloc_copy(X, X->orig, false);
+    if (st == PASTA_OK) {
+        e = cudaMalloc(&X->partials, kPartialsCap * sizeof(double));
+        if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(partials)");
+        X->partials_cap = kPartialsCap;
+    }
+    if (st == PASTA_OK) {
+        const size_t arr = (size_t)X->nnz_pad * 4;
+        e = cudaMemsetAsync(X->orig.block, 0, arr * (size_t)(order + 1), s);
+        for (int k = 0; k < order && e == cudaSuccess && nnz > 0; ++k)
+            e = cudaMemcpyAsync(X->orig.idx[k], d_idx[k], nnz * 4, cudaMemcpyDeviceToDevice, s);
+        if (e == cudaSuccess && nnz > 0)
+            e = cudaMemcpyAsync(X->orig.val, d_val, nnz * 4, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "copy-in");
+    }
+    if (st == PASTA_OK) X->orig.present = true;
+    if (st == PASTA_OK && !(flags & PASTA_CREATE_NO_VALIDATE)) {
+        uint64_t bi = 0, bv = 0;
+        st = validate_coo(X, stream, &bi, &bv);
+        if (st == PASTA_OK && bi) {
+            set_error("%llu index entries are >= their mode size", (unsigned long long)bi);
+            st = PASTA_ERR_INDEX_OOB;
+        } else if (st == PASTA_OK && bv) {
+            set_error("%llu values are NaN or Inf", (unsigned long long)bv);
+            st = PASTA_ERR_NONFINITE;
+        }
+    }
+    if (st != PASTA_OK) {
+        pasta_coo_destroy(X);
+        return st;
+    }
+    *out = X;
+    return PASTA_OK;
+}
+
+pasta_status pasta_coo_destroy(pasta_coo X) {
+    if (!X) return PASTA_OK;
+    cudaDeviceSynchronize();
+    free_copy(X->orig);
+    for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(X->sorted[k]);
+    if (X->partials) cudaFree(X->partials);
+    delete X;
+    return PASTA_OK;
+}
+
+pasta_status pasta_coo_info(pasta_coo X, int *order, uint64_t *dims, uint64_t *nnz) {
+    if (!X) {
+        set_error("X is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (order) *order = X->order;
+    if (dims)
+        for (int k = 0; k < X->order; ++k) dims[k] = X->dims[k];
+    if (nnz) *nnz = X->nnz;
+    return PASTA_OK;
+}
+
+pasta_status pasta_coo_sort_by_mode(pasta_coo X, int mode, void *stream) {
+    if (!X || mode < 0 || mode >= X->order) {
+        set_error("bad handle or mode");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    StoredCopy &c = X->sorted[mode];
+    if (c.present) return PASTA_OK;
+    pasta_status st = alloc_copy(X, c, true);
+    if (st != PASTA_OK) return st;
+    st = sort_copy(X, mode, static_cast<cudaStream_t>(stream));
+    if (st != PASTA_OK) {
+        cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+        free_copy(c);
+        return st;
+    }
+    c.present = true;
+    return PASTA_OK;
+}
+
+pasta_status pasta_coo_view(pasta_coo X, int mode, const uint32_t **d_idx, const float **d_val,
+                            const uint32_t **d_perm) {
+    if (!X || mode < -1 || mode >= X->order) {
+        set_error("bad handle or mode");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    const StoredCopy &c = mode < 0 ? X->orig : X->sorted[mode];
+    if (!c.present) {
+        set_error("mode %d has no sorted copy", mode);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    if (d_idx)
+        for (int k = 0; k < X->order; ++k) d_idx[k] = c.idx[k];
+    if (d_val) *d_val = c.val;
+    if (d_perm) *d_perm = c.perm;
+    return PASTA_OK;
+}
+
+pasta_status pasta_coo_copy_out(pasta_coo X, int mode, uint32_t *const *d_idx_out,
+                                float *d_val_out, uint32_t *d_perm_out, void *stream) {
+    if (!X || mode < -1 || mode >= X->order || (mode < 0 && d_perm_out)) {
+        set_error("bad handle or mode");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    const StoredCopy &c = mode < 0 ? X->orig : X->sorted[mode];
+    if (!c.present) {
+        set_error("mode %d has no sorted copy", mode);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = (size_t)X->nnz * 4;
+    if (bytes == 0) return PASTA_OK;
+    if (d_idx_out)
+        for (int k = 0; k < X->order; ++k)
+            if (d_idx_out[k])
+                PASTA_CUDA(cudaMemcpyAsync(d_idx_out[k], c.idx[k], bytes, cudaMemcpyDeviceToDevice, s));
+    if (d_val_out) PASTA_CUDA(cudaMemcpyAsync(d_val_out, c.val, bytes, cudaMemcpyDeviceToDevice, s));
+    if (d_perm_out) PASTA_CUDA(cudaMemcpyAsync(d_perm_out, c.perm, bytes, cudaMemcpyDeviceToDevice, s));
+    return PASTA_OK;
+}
+
+static pasta_status check_factors(pasta_coo X, const void *const *d_U, int dt, int R, int skip) {
+    if (!X) {
+        set_error("X is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (!ok_dtype(dt)) {
+        set_error("unknown dtype %d", dt);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (R < 1 || R > PASTA_MAX_RANK) {
+        set_error("R = %d out of [1, %d]", R, PASTA_MAX_RANK);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (!d_U) {
+        set_error("d_U is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < X->order; ++k)
+        if (k != skip && !d_U[k]) {
+            set_error("d_U[%d] is NULL", k);
+            return PASTA_ERR_INVALID_ARG;
+        }
+    return PASTA_OK;
+}
+
+pasta_status pasta_mttkrp(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int mode,
+                          int R, void *d_M, void *stream) {
+    if (X && (mode < 0 || mode >= X->order)) {
+        set_error("mode %d out of range", mode);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    pasta_status st = check_factors(X, d_U, u_dtype, R, mode);
+    if (st != PASTA_OK) return st;
+    if (!d_M) {
+        set_error("d_M is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (!X->sorted[mode].present) {
+        set_error("mode %d has no sorted copy (call pasta_coo_sort_by_mode)", mode);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    return launch_mttkrp(X, X->sorted[mode], d_U, u_dtype, mode, R, d_M,
+                         static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_cp_loss_fwd(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int R,
+                               int mode, double *d_loss, void *d_resid, void *stream) {
+    pasta_status st = check_factors(X, d_U, u_dtype, R, -1);
+    if (st != PASTA_OK) return st;
+    if (mode < -1 || mode >= X->order || !d_loss) {
+        set_error("bad mode or d_loss is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    const StoredCopy &c = mode < 0 ? X->orig : X->sorted[mode];
+    if (!c.present) {
+        set_error("mode %d has no sorted copy", mode);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    return launch_cp_loss_fwd(view_of(X, c), X->dims, X->num_sms, d_U, u_dtype, R, d_loss,
+                              d_resid, X->partials, X->partials_cap,
+                              static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int R,
+                               int mode, const double *d_gscale, void *const *d_G,
+                               void *stream) {
+    pasta_status st = check_factors(X, d_U, u_dtype, R, -1);
+    if (st != PASTA_OK) return st;
+    if (mode < -1 || mode >= X->order || !d_G) {
+        set_error("bad mode or d_G is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < X->order; ++k)
+        if (!d_G[k]) {
+            set_error("d_G[%d] is NULL", k);
+            return PASTA_ERR_INVALID_ARG;
+        }
+    const StoredCopy &c = mode < 0 ? X->orig : X->sorted[mode];
+    if (!c.present) {
+        set_error("mode %d has no sorted copy", mode);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    return launch_cp_loss_bwd(X, c, mode, d_U, u_dtype, R, d_gscale, d_G,
+                              static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_convert(const void *d_src, pasta_dtype src_dtype, void *d_dst,
+                           pasta_dtype dst_dtype, uint64_t n, void *stream) {
+    if (!ok_dtype(src_dtype) || !ok_dtype(dst_dtype) || (n > 0 && (!d_src || !d_dst))) {
+        set_error("bad dtype or NULL pointer");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    return launch_convert(d_src, src_dtype, d_dst, dst_dtype, n, static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

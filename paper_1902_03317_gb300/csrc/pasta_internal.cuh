@@ -1,0 +1,272 @@
+// Internal declarations shared by the translation units of libpasta.
+// Not installed; the public boundary is include/pasta.h.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pasta.h"
+
+namespace pasta {
+
+constexpr int kMaxOrder = PASTA_MAX_ORDER;
+constexpr uint32_t kNoRow = 0xFFFFFFFFu;  // no open segment (indices are < 2^32 - 1)
+constexpr uint64_t kPadEntries = 1024;    // stored arrays are padded to this multiple
+
+// ---------------------------------------------------------------- errors ---
+
+void set_error(const char *fmt, ...);
+pasta_status cuda_fail(cudaError_t e, const char *where);
+
+#define PASTA_CUDA(call)                                         \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return ::pasta::cuda_fail(e_, #call); \
+    } while (0)
+
+// ----------------------------------------------------------------- handle ---
+
+// One stored copy of the tensor: SoA, every array padded to kPadEntries and
+// 256-byte aligned inside one allocation.
+struct StoredCopy {
+    uint32_t *idx[kMaxOrder] = {};
+    float *val = nullptr;
+    uint32_t *perm = nullptr;  // sorted position -> creation-order entry (sorted copies)
+    void *block = nullptr;     // the allocation holding all arrays
+    bool present = false;
+};
+
+}  // namespace pasta
+
+struct pasta_coo_s {
+    int order = 0;
+    uint64_t dims[PASTA_MAX_ORDER] = {};
+    uint64_t nnz = 0;
+    uint64_t nnz_pad = 0;
+    int device = 0;
+    int num_sms = 0;
+    pasta::StoredCopy orig;
+    pasta::StoredCopy sorted[PASTA_MAX_ORDER];
+    double *partials = nullptr;  // per-block FP64 partial sums of the loss
+    int partials_cap = 0;
+};
+
+namespace pasta {
+
+// Read-only description of one stored copy, passed by value to kernels.
+struct CooView {
+    const uint32_t *idx[kMaxOrder];
+    const float *val;
+    uint64_t nnz;
+    int order;
+};
+
+CooView view_of(const pasta_coo_s *X, const StoredCopy &c);
+
+// --------------------------------------------------------- lane geometry ---
+//
+// Work is spread warp-wide with the lanes across the rank: a factor row of R
+// elements is cut into S "slots" of VEC elements (16 bytes on the fast path).
+// L = min(32, next_pow2(S)) lanes serve one entry and each lane owns J =
+// ceil(S / L) slots, so a warp works on G = 32 / L entries at a time, one per
+// lane group.  Each lane group walks a contiguous run ("tile") of the stream.
+struct Geometry {
+    int vec;     // elements per slot
+    int slots;   // S
+    int L;       // lanes per entry (power of two)
+    int lshift;  // log2(L)
+    int J;       // slots per lane
+    int tile;    // entries per lane-group tile (multiple of 4L)
+};
+
+Geometry make_geometry(int R, int vec, int elem_bytes);
+
+size_t dtype_size(pasta_dtype t);
+
+// ---------------------------------------------------------------- launchers --
+
+pasta_status validate_coo(const pasta_coo_s *X, void *stream, uint64_t *bad_index,
+                          uint64_t *bad_value);
+
+pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t stream);
+
+pasta_status launch_mttkrp(const pasta_coo_s *X, const StoredCopy &c, const void *const *U,
+                           pasta_dtype dt, int mode, int R, void *M, cudaStream_t stream);
+
+// Loss forward over an arbitrary stored copy; `partials` must hold at least
+// `partials_cap` doubles (the grid is capped to it).
+pasta_status launch_cp_loss_fwd(const CooView &v, const uint64_t *dims, int num_sms,
+                                const void *const *U, pasta_dtype dt, int R, double *loss,
+                                void *resid, double *partials, int partials_cap,
+                                cudaStream_t stream);
+
+pasta_status launch_cp_loss_bwd(const pasta_coo_s *X, const StoredCopy &c, int seg_mode,
+                                const void *const *U, pasta_dtype dt, int R,
+                                const double *gscale, void *const *G, cudaStream_t stream);
+
+pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,
+                            uint64_t n, cudaStream_t stream);
+
+// ------------------------------------------------------ device primitives ---
+
+template <typename T> struct AccOf { using type = float; };
+template <> struct AccOf<double> { using type = double; };
+
+// L2 policy for data streamed once (the COO arrays).
+__device__ __forceinline__ uint64_t policy_evict_first() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 16-byte streaming load of read-only data: no L1 allocation, evict-first in L2.
+__device__ __forceinline__ uint4 ld_stream_u4(const uint32_t *p, uint64_t pol) {
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+
+__device__ __forceinline__ float4 ld_stream_f4(const float *p, uint64_t pol) {
+    float4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v4.f32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
+}
+
+template <int Q> __device__ __forceinline__ uint32_t comp(const uint4 &v) {
+    return Q == 0 ? v.x : Q == 1 ? v.y : Q == 2 ? v.z : v.w;
+}
+template <int Q> __device__ __forceinline__ float compf(const float4 &v) {
+    return Q == 0 ? v.x : Q == 1 ? v.y : Q == 2 ? v.z : v.w;
+}
+
+// Load VEC consecutive factor elements (one slot) and widen to the
+// accumulation type.  The fast-path forms are 16-byte vector loads through
+// the read-only path.
+template <typename T, int VEC> struct RowLoad;
+
+template <> struct RowLoad<float, 4> {
+    __device__ __forceinline__ static void run(const float *p, float (&o)[4]) {
+        float4 v = __ldg(reinterpret_cast<const float4 *>(p));
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+};
+template <> struct RowLoad<float, 1> {
+    __device__ __forceinline__ static void run(const float *p, float (&o)[1]) { o[0] = __ldg(p); }
+};
+template <> struct RowLoad<__nv_bfloat16, 8> {
+    __device__ __forceinline__ static void run(const __nv_bfloat16 *p, float (&o)[8]) {
+        uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&w[i]);
+            float2 f = __bfloat1622float2(h);
+            o[2 * i] = f.x; o[2 * i + 1] = f.y;
+        }
+    }
+};
+template <> struct RowLoad<__nv_bfloat16, 1> {
+    __device__ __forceinline__ static void run(const __nv_bfloat16 *p, float (&o)[1]) {
+        o[0] = __bfloat162float(__ldg(p));
+    }
+};
+template <> struct RowLoad<__half, 8> {
+    __device__ __forceinline__ static void run(const __half *p, float (&o)[8]) {
+        uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+        const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            __half2 h = *reinterpret_cast<const __half2 *>(&w[i]);
+            float2 f = __half22float2(h);
+            o[2 * i] = f.x; o[2 * i + 1] = f.y;
+        }
+    }
+};
+template <> struct RowLoad<__half, 1> {
+    __device__ __forceinline__ static void run(const __half *p, float (&o)[1]) {
+        o[0] = __half2float(__ldg(p));
+    }
+};
+template <> struct RowLoad<double, 2> {
+    __device__ __forceinline__ static void run(const double *p, double (&o)[2]) {
+        double2 v = __ldg(reinterpret_cast<const double2 *>(p));
+        o[0] = v.x; o[1] = v.y;
+    }
+};
+template <> struct RowLoad<double, 1> {
+    __device__ __forceinline__ static void run(const double *p, double (&o)[1]) { o[0] = __ldg(p); }
+};
+
+// Add VEC accumulators into global memory without reading the old value.
+// The 4-wide FP32 form is one red.global.add.v4.f32 (16-byte aligned).
+template <typename A, int VEC> struct RedAdd;
+template <> struct RedAdd<float, 4> {
+    __device__ __forceinline__ static void run(float *d, const float (&a)[4]) {
+        asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d), "f"(a[0]), "f"(a[1]),
+                     "f"(a[2]), "f"(a[3]));
+    }
+};
+template <> struct RedAdd<float, 8> {
+    __device__ __forceinline__ static void run(float *d, const float (&a)[8]) {
+        asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d), "f"(a[0]), "f"(a[1]),
+                     "f"(a[2]), "f"(a[3]));
+        asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d + 4), "f"(a[4]),
+                     "f"(a[5]), "f"(a[6]), "f"(a[7]));
+    }
+};
+template <> struct RedAdd<float, 1> {
+    __device__ __forceinline__ static void run(float *d, const float (&a)[1]) {
+        asm volatile("red.global.add.f32 [%0], %1;" ::"l"(d), "f"(a[0]));
+    }
+};
+template <> struct RedAdd<double, 2> {
+    __device__ __forceinline__ static void run(double *d, const double (&a)[2]) {
+        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(d), "d"(a[0]));
+        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(d + 1), "d"(a[1]));
+    }
+};
+template <> struct RedAdd<double, 1> {
+    __device__ __forceinline__ static void run(double *d, const double (&a)[1]) {
+        asm volatile("red.global.add.f64 [%0], %1;" ::"l"(d), "d"(a[0]));
+    }
+};
+
+// Plain (non-atomic) store of VEC accumulators.
+template <typename A, int VEC> struct Store;
+template <> struct Store<float, 4> {
+    __device__ __forceinline__ static void run(float *d, const float (&a)[4]) {
+        asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d), "f"(a[0]), "f"(a[1]),
+                     "f"(a[2]), "f"(a[3]));
+    }
+};
+template <> struct Store<float, 8> {
+    __device__ __forceinline__ static void run(float *d, const float (&a)[8]) {
+        asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d), "f"(a[0]), "f"(a[1]),
+                     "f"(a[2]), "f"(a[3]));
+        asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(d + 4), "f"(a[4]), "f"(a[5]),
+                     "f"(a[6]), "f"(a[7]));
+    }
+};
+template <> struct Store<float, 1> {
+    __device__ __forceinline__ static void run(float *d, const float (&a)[1]) {
+        asm volatile("st.global.f32 [%0], %1;" ::"l"(d), "f"(a[0]));
+    }
+};
+template <> struct Store<double, 2> {
+    __device__ __forceinline__ static void run(double *d, const double (&a)[2]) {
+        asm volatile("st.global.v2.f64 [%0], {%1,%2};" ::"l"(d), "d"(a[0]), "d"(a[1]));
+    }
+};
+template <> struct Store<double, 1> {
+    __device__ __forceinline__ static void run(double *d, const double (&a)[1]) {
+        asm volatile("st.global.f64 [%0], %1;" ::"l"(d), "d"(a[0]));
+    }
+};
+
+}  // namespace pasta

@@ -1,0 +1,104 @@
+"""Full-size workloads, in the launch configuration the benchmark times,
+checked on sampled output rows that the oracle computes from the entries
+that reach them (the generated tensor, never the GPU's sorted copy).
+
+Sampled rows per mode: the heaviest row (the accuracy worst case), a few
+random touched rows and, where one exists, an untouched row (must be 0).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1902_03317_gb300 as pasta
+from paper_1902_03317_gb300 import synth
+from tests import _gpu as G
+
+pytestmark = [pytest.mark.gpu, pytest.mark.fullsize]
+
+
+def sample_rows(ix: np.ndarray, dim: int, rng, k: int = 6):
+    counts = np.bincount(ix, minlength=dim)
+    touched = np.flatnonzero(counts)
+    rows = [int(np.argmax(counts))]
+    rows += [int(r) for r in rng.choice(touched, size=min(k, touched.size), replace=False)]
+    untouched = np.flatnonzero(counts == 0)
+    if untouched.size:
+        rows.append(int(untouched[rng.integers(0, untouched.size)]))
+    return sorted(set(rows))
+
+
+def subset(idx, val, mode, rows, dim):
+    lut = np.zeros(dim, dtype=bool)
+    lut[rows] = True
+    keep = lut[idx[mode]]
+    return [ix[keep] for ix in idx], val[keep]
+
+
+def mttkrp_rows_check(name, dtypes, max_heavy=None):
+    wl = synth.WORKLOADS[name]
+    Xd = synth.generate(wl, device=G.DEV)
+    X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
+    X.sort_all()
+    idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
+    val = Xd.val.cpu().numpy().astype(np.float64)
+    del Xd
+    rng = np.random.default_rng(0)
+    for dtype in dtypes:
+        master = synth.factors_for(wl)
+        dev = [u.to(dtype).to(G.DEV).contiguous() for u in master]
+        rounded = [u.to(dtype).double().numpy() for u in master]
+        for n in range(wl.order):
+            M = pasta.mttkrp(X, dev, n)
+            rows = sample_rows(idx[n], wl.dims[n], rng)
+            if max_heavy is not None:
+                rows = rows[:max_heavy] if wl.dims[n] <= max_heavy else rows
+            sidx, sval = subset(idx, val, n, rows, wl.dims[n])
+            ref = oracle.mttkrp(wl.dims, sidx, sval, rounded, n)[rows]
+            got = M[torch.tensor(rows, device=G.DEV)].cpu().numpy()
+            err = G.rel_err(got, ref)
+            assert err < G.FP32_TOL, f"{name} {dtype} mode {n}: {err}"
+            if dtype != torch.float32:
+                ref_m = oracle.mttkrp(wl.dims, sidx, sval, [u.numpy() for u in master], n)[rows]
+                assert G.rel_err(got, ref_m) < G.LOWP_TOL
+    X.close()
+    torch.cuda.empty_cache()
+
+
+def test_zipf3d_100M_fp32():
+    mttkrp_rows_check("zipf3d", [torch.float32, torch.bfloat16])
+
+
+def test_zipf4d_50M_fp32_and_bf16():
+    mttkrp_rows_check("zipf4d", [torch.float32, torch.bfloat16])
+
+
+def test_zipf5d_200M_bf16():
+    mttkrp_rows_check("zipf5d", [torch.bfloat16], max_heavy=3)
+
+
+def test_cploss3d_20M_loss_and_grad():
+    wl = synth.WORKLOADS["cploss3d"]
+    Xd = synth.generate(wl, device=G.DEV)
+    X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
+    X.sort_by_mode(0)
+    idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
+    val = Xd.val.cpu().numpy().astype(np.float64)
+    del Xd
+    rng = np.random.default_rng(1)
+    for dtype in (torch.float32, torch.bfloat16):
+        master = synth.factors_for(wl)
+        dev = [u.to(dtype).to(G.DEV).contiguous() for u in master]
+        rounded = [u.to(dtype).double().numpy() for u in master]
+        loss = pasta.cp_loss_fwd(X, dev, 0).item()
+        ref = oracle.cp_loss(wl.dims, idx, val, rounded)
+        assert abs(loss - ref) <= G.FP32_TOL * ref
+        grads = pasta.cp_loss_bwd(X, dev, 0)
+        for k in range(3):
+            rows = sample_rows(idx[k], wl.dims[k], rng)
+            sidx, sval = subset(idx, val, k, rows, wl.dims[k])
+            refg = oracle.cp_grad(wl.dims, sidx, sval, rounded)[k][rows]
+            got = grads[k][torch.tensor(rows, device=G.DEV)].cpu().numpy()
+            assert G.rel_err(got, refg) < G.FP32_TOL, (dtype, k)
+    X.close()
+    torch.cuda.empty_cache()

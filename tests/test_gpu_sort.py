@@ -1,0 +1,86 @@
+"""Mode-order sort (Sec. 5.2.2) on the GPU vs the oracle's stable lexsort.
+
+Where the packed key holds every mode (at most 64 bits), the stable sort is
+unique and the permutation must match bit for bit.  Where the key is cut to
+its leading 64 bits, only the order of the fully included modes is fixed:
+that part is compared, the rest is checked to be a valid permutation.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests import _gpu as G
+
+pytestmark = pytest.mark.gpu
+
+
+CASES = [
+    ("uniform3d_200", 20_000, (200, 200, 200)),
+    ("zipf3d", 50_000, (5000, 3000, 1000)),
+    ("zipf4d", 60_000, (3000, 3000, 300, 60)),      # duplicates kept
+    ("zipf5d", 40_000, (8, 2000, 500, 100, 10)),    # duplicates kept
+]
+
+
+@pytest.mark.parametrize("name,nnz,dims", CASES)
+def test_sorted_copies_match_oracle_exactly(name, nnz, dims):
+    Xh = G.synth.generate(G.small(name, nnz, dims))
+    idx, val = G.host(Xh)
+    X = G.to_device(Xh)
+    for mode in range(len(dims)):
+        X.sort_by_mode(mode)
+        sidx, sval, perm = X.copy_out(mode)
+        perm = perm.cpu().numpy().astype(np.int64)
+        np.testing.assert_array_equal(perm, oracle.sort_perm(idx, mode))
+        for k in range(len(dims)):
+            np.testing.assert_array_equal(sidx[k].cpu().numpy().astype(np.uint32), idx[k][perm])
+        np.testing.assert_array_equal(sval.cpu().numpy(), val[perm].astype(np.float32))
+    # the creation-order copy is untouched
+    oidx, oval, _ = X.copy_out(-1)
+    np.testing.assert_array_equal(oidx[1].cpu().numpy().astype(np.uint32), idx[1])
+    X.close()
+
+
+def test_key_cut_to_64_bits_keeps_leading_modes_sorted():
+    # 3 + 24 + 21 + 17 + 10 = 75 bits: the key holds modes 0,1,2 and the top
+    # 16 bits of mode 3 when sorting for mode 0.
+    dims = (8, 10_000_000, 2_000_000, 100_000, 1_000)
+    Xh = G.synth.generate(G.small("zipf5d", 30_000, dims))
+    idx, _ = G.host(Xh)
+    X = G.to_device(Xh)
+    for mode in range(5):
+        X.sort_by_mode(mode)
+        _, _, perm = X.copy_out(mode)
+        perm = perm.cpu().numpy().astype(np.int64)
+        assert np.array_equal(np.sort(perm), np.arange(perm.size))
+        order = oracle.mode_order(5, mode)
+        bits = [max(0, int(dims[k] - 1).bit_length()) for k in order]
+        full = []
+        used = 0
+        for k, b in zip(order, bits):
+            if used + b > 64:
+                break
+            full.append(k)
+            used += b
+        # the leading fully-included modes are in lexicographic order
+        keys = np.stack([idx[k][perm].astype(np.int64) for k in full], axis=1)
+        lex = np.lexsort(keys.T[::-1])
+        assert np.array_equal(lex, np.arange(perm.size)), f"mode {mode} not sorted"
+        np.testing.assert_array_equal(idx[mode][perm], np.sort(idx[mode]))
+    X.close()
+
+
+@pytest.mark.parametrize("nnz", [0, 1, 2, 5, 4095, 4096, 4097])
+def test_sort_small_and_ragged(nnz):
+    dims = (7, 5, 3)
+    g = torch.Generator().manual_seed(nnz)
+    Xh = G.synth.Tensor(None, dims, [torch.randint(0, d, (nnz,), generator=g, dtype=torch.int32) for d in dims],
+                        torch.rand(nnz, generator=g))
+    idx, _ = G.host(Xh)
+    X = G.to_device(Xh)
+    for mode in range(3):
+        X.sort_by_mode(mode)
+        _, _, perm = X.copy_out(mode)
+        np.testing.assert_array_equal(perm.cpu().numpy().astype(np.int64), oracle.sort_perm(idx, mode))
+    X.close()
