@@ -7,8 +7,8 @@ values, R = 32 FP32 factors (synthetic, seeded; stands in for the paper's
 FROSTT-style tensors).
 
 One timed step = one pass of the hot path over the tensor: MTTKRP on every
-mode (each on its mode-sorted copy) followed by the CP-loss forward and
-backward (all modes in one pass).  The mode sorts are preprocessing: they run
+mode (each on its mode-sorted copy) followed by the CP-loss forward (over the
+mode-0 copy) and backward (one pass per mode over that mode's sorted copy).  The mode sorts are preprocessing: they run
 once before timing, as the paper's "provided" sort does, and their time is
 reported under "preprocess".  `value` = N modes x nnz / (MTTKRP part of the
 step), summed over ranks, with device time taken by CUDA events on the
@@ -200,7 +200,7 @@ def run_own(args, rank, world, local):
             if ev is not None:
                 ev[2 * n + 1].record(stream)
         pasta.cp_loss_fwd(X, Us, 0)
-        pasta.cp_loss_bwd(X, Us, 0)
+        pasta.cp_loss_bwd(X, Us, -2)
         if ev is not None:
             ev[2 * N].record(stream)
 
@@ -253,14 +253,14 @@ def run_own(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc(wl), "step": "MTTKRP every mode + CP-loss fwd + bwd (mode-0 copy)",
+        "config": {"workload": workload_desc(wl), "step": "MTTKRP every mode + CP-loss fwd (mode-0 copy) + bwd (one pass per mode over its sorted copy)",
                    "l2": "no flush: inputs larger than L2 (COO stream 1.6 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": roofline,
         "breakdown_ms": {"mttkrp_per_mode": [round(x, 4) for x in per_mode_ms],
                          "loss_fwd_bwd": round(loss_ms_mean, 4)},
         "preprocess": {"sort_ms_per_mode": [round(x, 2) for x in t_sort]},
-        "gpu_launches": args.steps * (N + 2 + 1),
+        "gpu_launches": args.steps * (N + 2 + N),
         "clocks": clk,
     }
     del Xd
@@ -288,25 +288,30 @@ def loss_compare(pasta, synth, dev, args):
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     X.sort_by_mode(0)
     del Xd
-    out = {"workload": workload_desc(wl)}
+    X.sort_all()
+    out = {"workload": workload_desc(wl), "path": "autograd CPLoss, forward over the mode-0 copy"}
     stream = torch.cuda.current_stream()
-    for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
-        Us = [u.requires_grad_(True) for u in synth.factors_for(wl, device=dev, dtype=dt)]
-        for _ in range(3):
-            pasta.cp_loss(X, Us, 0).backward()
-        reps = max(5, args.steps)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record(stream)
-        for _ in range(reps):
-            for u in Us:
-                u.grad = None
-            pasta.cp_loss(X, Us, 0).backward()
-        b.record(stream)
-        torch.cuda.synchronize()
-        out[f"{name}_fwd_bwd_ms"] = round(a.elapsed_time(b) / reps, 4)
-    out["bf16_speedup"] = round(out["fp32_fwd_bwd_ms"] / out["bf16_fwd_bwd_ms"], 3)
+    for bwd, tag in ((-2, "per_mode"), (0, "one_pass")):
+        for name, dt in (("fp32", torch.float32), ("bf16", torch.bfloat16)):
+            Us = [u.requires_grad_(True) for u in synth.factors_for(wl, device=dev, dtype=dt)]
+            for _ in range(3):
+                pasta.cp_loss(X, Us, bwd).backward()
+            reps = max(5, args.steps)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record(stream)
+            for _ in range(reps):
+                for u in Us:
+                    u.grad = None
+                pasta.cp_loss(X, Us, bwd).backward()
+            b.record(stream)
+            torch.cuda.synchronize()
+            out[f"{name}_fwd_bwd_ms_{tag}"] = round(a.elapsed_time(b) / reps, 4)
+    best = {n: min(out[f"{n}_fwd_bwd_ms_per_mode"], out[f"{n}_fwd_bwd_ms_one_pass"]) for n in ("fp32", "bf16")}
+    out["fp32_fwd_bwd_ms"] = best["fp32"]
+    out["bf16_fwd_bwd_ms"] = best["bf16"]
+    out["bf16_speedup"] = round(best["fp32"] / best["bf16"], 3)
     X.close()
     torch.cuda.empty_cache()
     return out

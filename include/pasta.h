@@ -184,13 +184,20 @@ pasta_status pasta_cp_loss_fwd(pasta_coo X, const void *const *d_U, pasta_dtype 
  *     G_k(i, r) = -g * sum_{m : i_k(m) = i} e(m) * prod_{j != k} U_j(i_j(m), r)
  * (-g times the mode-k MTTKRP of the residual tensor).  e(m) is recomputed
  * from the factors.
- *   mode     copy to stream, as for pasta_cp_loss_fwd; the sorted mode's
- *            gradient is reduced in registers along runs of equal index, the
- *            other modes' with vector atomics
+ *   mode     -1: one pass over the creation-order copy, every gradient
+ *            added with vector atomics;
+ *            n in [0, N): one pass over the mode-n sorted copy, G_n reduced
+ *            in registers along runs of equal index, the other modes with
+ *            vector atomics;
+ *            PASTA_BWD_PER_MODE (-2): N passes, pass k over the mode-k sorted
+ *            copy computing only G_k by run reduction (no atomics on hot
+ *            rows; every sorted copy must exist)
  *   d_gscale device FP64 scalar g (NULL means g = 1)
  *   d_G      host array of N device pointers to dims[k] x R row-major outputs,
  *            FP32 (FP64 for PASTA_F64 factors); all overwritten
  */
+#define PASTA_BWD_PER_MODE (-2)
+
 pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int R,
                                int mode, const double *d_gscale, void *const *d_G, void *stream);
 

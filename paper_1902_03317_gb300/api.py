@@ -186,11 +186,19 @@ def cp_loss_fwd(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = -1,
     return (loss, resid) if want_resid else loss
 
 
-def cp_loss_bwd(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = -1,
+BWD_PER_MODE = -2
+
+
+def cp_loss_bwd(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = BWD_PER_MODE,
                 gscale: torch.Tensor | None = None) -> list[torch.Tensor]:
-    """Gradient of ``gscale * loss`` for every factor, in one pass; FP32
-    (FP64 for FP64 factors) accumulators."""
-    if mode >= 0:
+    """Gradient of ``gscale * loss`` for every factor; FP32 (FP64 for FP64
+    factors) accumulators.  ``mode``: -1 one pass over the creation-order copy
+    (atomics), n one pass over the mode-n copy (mode n reduced along runs,
+    atomics for the others), -2 (default) one pass per mode over its own
+    sorted copy (run reduction only; no contention on hot rows)."""
+    if mode == BWD_PER_MODE:
+        X.sort_all()
+    elif mode >= 0:
         X.sort_by_mode(mode)
     ptrs, dt, R = _factor_ptrs(X, Us)
     G = [torch.empty((d, R), dtype=acc_dtype(dt), device=X.device) for d in X.dims]
@@ -221,10 +229,13 @@ class CPLoss(torch.autograd.Function):
     """loss = 1/2 sum_m (x_m - sum_r prod_k U_k(i_k(m), r))^2 over the stored
     entries of X, with hand-written forward and backward kernels.
 
-    ``CPLoss.apply(X, mode, *Us)``: ``mode`` selects the stored copy streamed
-    (-1 = creation order; a sorted mode lets the backward reduce that mode's
-    gradient along runs).  Returns an FP64 0-d tensor; gradients come back in
-    each factor's dtype (FP32 accumulation, converted on the device)."""
+    ``CPLoss.apply(X, mode, *Us)``: ``mode`` selects how the stored entries
+    are streamed: -1 creation order; n the mode-n sorted copy (the backward
+    reduces mode n along runs, the others with atomics); -2 (default of
+    ``cp_loss``) the forward over the mode-0 copy and the backward as one pass
+    per mode over each mode's sorted copy.  Returns an FP64 0-d tensor;
+    gradients come back in each factor's dtype (FP32 accumulation, converted
+    on the device)."""
 
     @staticmethod
     def forward(ctx, X: CooTensor, mode: int, *Us: torch.Tensor):
@@ -232,7 +243,7 @@ class CPLoss(torch.autograd.Function):
         ctx.X = X
         ctx.mode = mode
         ctx.save_for_backward(*Us)
-        return cp_loss_fwd(X, Us, mode)
+        return cp_loss_fwd(X, Us, 0 if mode == BWD_PER_MODE else mode)
 
     @staticmethod
     def backward(ctx, grad_out: torch.Tensor):
@@ -244,6 +255,6 @@ class CPLoss(torch.autograd.Function):
         return (None, None, *grads)
 
 
-def cp_loss(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = -1) -> torch.Tensor:
+def cp_loss(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = BWD_PER_MODE) -> torch.Tensor:
     """Differentiable sparse CP loss (see CPLoss)."""
     return CPLoss.apply(X, mode, *Us)

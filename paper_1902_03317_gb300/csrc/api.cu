@@ -402,7 +402,7 @@ pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype 
                                void *stream) {
     pasta_status st = check_factors(X, d_U, u_dtype, R, -1);
     if (st != PASTA_OK) return st;
-    if (mode < -1 || mode >= X->order || !d_G) {
+    if (mode < PASTA_BWD_PER_MODE || mode >= X->order || !d_G) {
         set_error("bad mode or d_G is NULL");
         return PASTA_ERR_INVALID_ARG;
     }
@@ -411,12 +411,14 @@ pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype 
             set_error("d_G[%d] is NULL", k);
             return PASTA_ERR_INVALID_ARG;
         }
-    const StoredCopy &c = mode < 0 ? X->orig : X->sorted[mode];
-    if (!c.present) {
-        set_error("mode %d has no sorted copy", mode);
-        return PASTA_ERR_NOT_SORTED;
+    for (int k = 0; k < X->order; ++k) {
+        const bool need = mode == PASTA_BWD_PER_MODE || mode == k;
+        if (need && !X->sorted[k].present) {
+            set_error("mode %d has no sorted copy", k);
+            return PASTA_ERR_NOT_SORTED;
+        }
     }
-    return launch_cp_loss_bwd(X, c, mode, d_U, u_dtype, R, d_gscale, d_G,
+    return launch_cp_loss_bwd(X, mode, d_U, u_dtype, R, d_gscale, d_G,
                               static_cast<cudaStream_t>(stream));
 }
 

@@ -41,7 +41,8 @@ struct LossArgs {
     const double *gscale;            // backward only, optional
     uint64_t nnz;
     int order;
-    int seg;  // backward: position 0 is the sorted mode, reduced along runs
+    int seg;       // backward: position 0 is the sorted mode, reduced along runs
+    int seg_only;  // backward: compute only position 0's gradient (no atomics)
     int R, S, L, lshift, tile;
 };
 
@@ -294,7 +295,7 @@ struct BwdBody {
 #pragma unroll
                         for (int e = 0; e < VEC; ++e) acc[j][e] += t[j][e];
                 }
-            } else {
+            } else if (!a.seg_only) {
                 A *dst = a.G[k] + (uint64_t)iq.v[k] * (uint64_t)a.R;
 #pragma unroll
                 for (int j = 0; j < J; ++j)
@@ -370,19 +371,28 @@ pasta_status fwd_run(const CooView &v, int num_sms, const void *const *U, int R,
 }
 
 template <typename T, int VEC, int J, int NM>
-pasta_status bwd_run(const pasta_coo_s *X, const CooView &v, int seg_mode, const void *const *U,
-                     int R, const Geometry &g, const double *gscale, void *const *G,
-                     cudaStream_t s) {
+pasta_status bwd_run(const pasta_coo_s *X, int seg_mode, const void *const *U, int R,
+                     const Geometry &g, const double *gscale, void *const *G, cudaStream_t s) {
     using A = typename AccOf<T>::type;
     for (int k = 0; k < X->order; ++k)
         PASTA_CUDA(cudaMemsetAsync(G[k], 0, (size_t)X->dims[k] * (size_t)R * sizeof(A), s));
-    if (v.nnz == 0) return PASTA_OK;
-    LossArgs<T, NM> a = make_args<T, NM>(v, seg_mode < 0 ? 0 : seg_mode, U, G, R, g);
-    a.gscale = gscale;
-    a.seg = seg_mode >= 0 ? 1 : 0;
-    const int blocks = grid_for(k_loss_bwd<T, VEC, J, NM>, v.nnz, g, X->num_sms, 0);
-    k_loss_bwd<T, VEC, J, NM><<<blocks, kThreads, 0, s>>>(a);
-    PASTA_CUDA(cudaGetLastError());
+    if (X->nnz == 0) return PASTA_OK;
+    // seg_mode >= 0: one pass over that mode's sorted copy; -1: one pass over
+    // the creation-order copy (atomics for every mode); -2: one pass per mode,
+    // each over its own sorted copy, reducing only that mode's gradient.
+    const int passes = seg_mode == -2 ? X->order : 1;
+    for (int p = 0; p < passes; ++p) {
+        const int mode = seg_mode == -2 ? p : seg_mode;
+        const StoredCopy &c = mode < 0 ? X->orig : X->sorted[mode];
+        const CooView v = view_of(X, c);
+        LossArgs<T, NM> a = make_args<T, NM>(v, mode < 0 ? 0 : mode, U, G, R, g);
+        a.gscale = gscale;
+        a.seg = mode >= 0 ? 1 : 0;
+        a.seg_only = seg_mode == -2 ? 1 : 0;
+        const int blocks = grid_for(k_loss_bwd<T, VEC, J, NM>, v.nnz, g, X->num_sms, 0);
+        k_loss_bwd<T, VEC, J, NM><<<blocks, kThreads, 0, s>>>(a);
+        PASTA_CUDA(cudaGetLastError());
+    }
     return PASTA_OK;
 }
 
@@ -506,14 +516,13 @@ pasta_status launch_cp_loss_fwd(const CooView &v, const uint64_t *dims, int num_
                            cap, s);
 }
 
-pasta_status launch_cp_loss_bwd(const pasta_coo_s *X, const StoredCopy &c, int seg_mode,
-                                const void *const *U, pasta_dtype dt, int R,
-                                const double *gscale, void *const *G, cudaStream_t s) {
-    const CooView v = view_of(X, c);
-    const bool fast = fast_path(dt, R, v.order, U, G, nullptr);
+pasta_status launch_cp_loss_bwd(const pasta_coo_s *X, int seg_mode, const void *const *U,
+                                pasta_dtype dt, int R, const double *gscale, void *const *G,
+                                cudaStream_t s) {
+    const bool fast = fast_path(dt, R, X->order, U, G, nullptr);
     const int es = (int)dtype_size(dt);
     const Geometry g = make_geometry(R, fast ? 16 / es : 1, es);
-    return dispatch<BwdFn>(dt, fast, g.J, v.order, X, v, seg_mode, U, R, g, gscale, G, s);
+    return dispatch<BwdFn>(dt, fast, g.J, X->order, X, seg_mode, U, R, g, gscale, G, s);
 }
 
 pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,

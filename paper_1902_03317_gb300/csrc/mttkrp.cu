@@ -35,9 +35,27 @@ struct MttkrpArgs {
     int R, S, L, lshift, tile;
 };
 
+// Load this lane's four consecutive entries of a chunk: one 16-byte streamed
+// load per COO array (arrays are padded, so the load stays in bounds).
+template <int NM>
+__device__ __forceinline__ void load_chunk(const uint32_t *const (&idx)[NM], const float *val,
+                                           int nother, uint64_t my, bool ld, uint64_t pol,
+                                           uint32_t (&ci)[NM][4], float (&cv)[4]) {
+#pragma unroll
+    for (int k = 0; k < NM; ++k) {
+        uint4 w = make_uint4(0u, 0u, 0u, 0u);
+        if (ld && k <= nother) w = ld_stream_u4(idx[k] + my, pol);
+        ci[k][0] = w.x; ci[k][1] = w.y; ci[k][2] = w.z; ci[k][3] = w.w;
+    }
+    float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (ld) w = ld_stream_f4(val + my, pol);
+    cv[0] = w.x; cv[1] = w.y; cv[2] = w.z; cv[3] = w.w;
+}
+
 template <typename T, int VEC, int J, int NM>
 __global__ void __launch_bounds__(kThreads) k_mttkrp(const MttkrpArgs<T, NM> a) {
     using A = typename AccOf<T>::type;
+    using RawT = typename Raw<T, VEC>::type;
     constexpr unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const int L = a.L;
@@ -84,61 +102,75 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(const MttkrpArgs<T, NM> a) 
             }
         };
 
+        // COO words of the current chunk; the next chunk's are requested
+        // before the current one is processed.
+        uint32_t ci[NM][4];
+        float cv[4];
+        {
+            const uint64_t my = t0 + 4u * (uint64_t)lig;
+            load_chunk<NM>(a.idx, a.val, a.nother, my, my < t1, pol, ci, cv);
+        }
         for (int c = 0; c < a.tile; c += chunk) {
             const uint64_t base = t0 + (uint64_t)c;
             if (!__any_sync(FULL, base < t1)) break;
-            // This lane's four consecutive entries of the chunk, one 16-byte
-            // load per array (arrays are padded, so the load stays in bounds).
-            const uint64_t my = base + 4u * (uint64_t)lig;
-            const bool ld = my < t1;
-            uint32_t ci[NM][4];
-            float cv[4];
-#pragma unroll
-            for (int k = 0; k < NM; ++k) {
-                uint4 w = make_uint4(0u, 0u, 0u, 0u);
-                if (ld && k <= a.nother) w = ld_stream_u4(a.idx[k] + my, pol);
-                ci[k][0] = w.x; ci[k][1] = w.y; ci[k][2] = w.z; ci[k][3] = w.w;
-            }
+            uint32_t ni[NM][4];
+            float nv[4];
             {
-                float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ld) w = ld_stream_f4(a.val + my, pol);
-                cv[0] = w.x; cv[1] = w.y; cv[2] = w.z; cv[3] = w.w;
+                const uint64_t my = base + (uint64_t)chunk + 4u * (uint64_t)lig;
+                load_chunk<NM>(a.idx, a.val, a.nother, my, c + chunk < a.tile && my < t1, pol, ni, nv);
             }
 
             for (int src = 0; src < L; ++src) {
+                // Phase A: indices, values and every gathered row of the four
+                // entries held by lane `src` of the group, all loads in flight
+                // before any is used.
+                uint32_t io[4];
+                float v[4];
+                bool ok[4];
+                RawT rows[4][NM > 1 ? NM - 1 : 1][J];
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
-                    const uint64_t m = base + 4u * (uint64_t)src + (uint64_t)q;
-                    const bool ok = m < t1;  // uniform within the lane group
-                    const uint32_t io = __shfl_sync(FULL, ci[0][q], src, L);
-                    const float v = __shfl_sync(FULL, cv[q], src, L);
-                    A t[J][VEC];
-#pragma unroll
-                    for (int j = 0; j < J; ++j)
-#pragma unroll
-                        for (int e = 0; e < VEC; ++e) t[j][e] = A(v);
+                    ok[q] = base + 4u * (uint64_t)src + (uint64_t)q < t1;  // uniform per group
+                    io[q] = __shfl_sync(FULL, ci[0][q], src, L);
+                    v[q] = __shfl_sync(FULL, cv[q], src, L);
 #pragma unroll
                     for (int k = 1; k < NM; ++k) {
                         if (k > a.nother) continue;
                         const uint32_t ik = __shfl_sync(FULL, ci[k][q], src, L);
-                        if (!ok) continue;
                         const T *row = a.U[k] + (uint64_t)ik * (uint64_t)a.R;
+#pragma unroll
+                        for (int j = 0; j < J; ++j)
+                            if (ok[q] && act[j]) rows[q][k - 1][j] = load_raw<T, VEC>(row + slot[j] * VEC);
+                    }
+                }
+                // Phase B: Hadamard product scaled by the value, then the run
+                // reduction along equal output rows.
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (!ok[q]) continue;
+                    A t[J][VEC];
+#pragma unroll
+                    for (int j = 0; j < J; ++j)
+#pragma unroll
+                        for (int e = 0; e < VEC; ++e) t[j][e] = A(v[q]);
+#pragma unroll
+                    for (int k = 1; k < NM; ++k) {
+                        if (k > a.nother) continue;
 #pragma unroll
                         for (int j = 0; j < J; ++j) {
                             if (!act[j]) continue;
                             A r[VEC];
-                            RowLoad<T, VEC>::run(row + slot[j] * VEC, r);
+                            widen<T, VEC>(rows[q][k - 1][j], r);
 #pragma unroll
                             for (int e = 0; e < VEC; ++e) t[j][e] *= r[e];
                         }
                     }
-                    if (!ok) continue;
-                    if (io != cur) {
+                    if (io[q] != cur) {
                         if (cur != kNoRow) {
                             flush(cur, first);
                             first = false;
                         }
-                        cur = io;
+                        cur = io[q];
 #pragma unroll
                         for (int j = 0; j < J; ++j)
 #pragma unroll
@@ -151,6 +183,12 @@ __global__ void __launch_bounds__(kThreads) k_mttkrp(const MttkrpArgs<T, NM> a) 
                     }
                 }
             }
+#pragma unroll
+            for (int k = 0; k < NM; ++k)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) ci[k][q] = ni[k][q];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) cv[q] = nv[q];
         }
         if (cur != kNoRow) flush(cur, true);
     }

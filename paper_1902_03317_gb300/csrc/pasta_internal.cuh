@@ -7,6 +7,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "pasta.h"
 
 namespace pasta {
@@ -102,9 +104,11 @@ pasta_status launch_cp_loss_fwd(const CooView &v, const uint64_t *dims, int num_
                                 void *resid, double *partials, int partials_cap,
                                 cudaStream_t stream);
 
-pasta_status launch_cp_loss_bwd(const pasta_coo_s *X, const StoredCopy &c, int seg_mode,
-                                const void *const *U, pasta_dtype dt, int R,
-                                const double *gscale, void *const *G, cudaStream_t stream);
+// seg_mode: >= 0 one pass over that sorted copy, -1 one pass over the
+// creation-order copy, -2 one pass per mode over each mode's sorted copy.
+pasta_status launch_cp_loss_bwd(const pasta_coo_s *X, int seg_mode, const void *const *U,
+                                pasta_dtype dt, int R, const double *gscale, void *const *G,
+                                cudaStream_t stream);
 
 pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,
                             uint64_t n, cudaStream_t stream);
@@ -202,6 +206,50 @@ template <> struct RowLoad<double, 2> {
 template <> struct RowLoad<double, 1> {
     __device__ __forceinline__ static void run(const double *p, double (&o)[1]) { o[0] = __ldg(p); }
 };
+
+// Split form of RowLoad for software pipelining: load_raw issues the load
+// (16 bytes on the fast path, kept as raw bits so a pending load costs four
+// registers whatever the element type), widen converts after it lands.
+template <typename T, int VEC> struct Raw { using type = uint4; };
+template <typename T> struct Raw<T, 1> { using type = T; };
+
+template <typename T, int VEC>
+__device__ __forceinline__ typename Raw<T, VEC>::type load_raw(const T *p) {
+    if constexpr (VEC == 1)
+        return __ldg(p);
+    else
+        return __ldg(reinterpret_cast<const uint4 *>(p));
+}
+
+template <typename T, int VEC>
+__device__ __forceinline__ void widen(const typename Raw<T, VEC>::type &r,
+                                      typename AccOf<T>::type (&o)[VEC]) {
+    if constexpr (VEC == 1) {
+        if constexpr (std::is_same<T, __nv_bfloat16>::value)
+            o[0] = __bfloat162float(r);
+        else if constexpr (std::is_same<T, __half>::value)
+            o[0] = __half2float(r);
+        else
+            o[0] = r;
+    } else if constexpr (std::is_same<T, float>::value) {
+        o[0] = __uint_as_float(r.x); o[1] = __uint_as_float(r.y);
+        o[2] = __uint_as_float(r.z); o[3] = __uint_as_float(r.w);
+    } else if constexpr (std::is_same<T, double>::value) {
+        o[0] = __hiloint2double((int)r.y, (int)r.x);
+        o[1] = __hiloint2double((int)r.w, (int)r.z);
+    } else {
+        const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float2 f;
+            if constexpr (std::is_same<T, __nv_bfloat16>::value)
+                f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[i]));
+            else
+                f = __half22float2(*reinterpret_cast<const __half2 *>(&w[i]));
+            o[2 * i] = f.x; o[2 * i + 1] = f.y;
+        }
+    }
+}
 
 // Add VEC accumulators into global memory without reading the old value.
 // The 4-wide FP32 form is one red.global.add.v4.f32 (16-byte aligned).

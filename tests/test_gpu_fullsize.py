@@ -81,7 +81,7 @@ def test_cploss3d_20M_loss_and_grad():
     wl = synth.WORKLOADS["cploss3d"]
     Xd = synth.generate(wl, device=G.DEV)
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
-    X.sort_by_mode(0)
+    X.sort_all()
     idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
     val = Xd.val.cpu().numpy().astype(np.float64)
     del Xd
@@ -93,12 +93,13 @@ def test_cploss3d_20M_loss_and_grad():
         loss = pasta.cp_loss_fwd(X, dev, 0).item()
         ref = oracle.cp_loss(wl.dims, idx, val, rounded)
         assert abs(loss - ref) <= G.FP32_TOL * ref
-        grads = pasta.cp_loss_bwd(X, dev, 0)
-        for k in range(3):
-            rows = sample_rows(idx[k], wl.dims[k], rng)
-            sidx, sval = subset(idx, val, k, rows, wl.dims[k])
-            refg = oracle.cp_grad(wl.dims, sidx, sval, rounded)[k][rows]
-            got = grads[k][torch.tensor(rows, device=G.DEV)].cpu().numpy()
-            assert G.rel_err(got, refg) < G.FP32_TOL, (dtype, k)
+        for bwd_mode in (0, -2):
+            grads = pasta.cp_loss_bwd(X, dev, bwd_mode)
+            for k in range(3):
+                rows = sample_rows(idx[k], wl.dims[k], rng)
+                sidx, sval = subset(idx, val, k, rows, wl.dims[k])
+                refg = oracle.cp_grad(wl.dims, sidx, sval, rounded)[k][rows]
+                got = grads[k][torch.tensor(rows, device=G.DEV)].cpu().numpy()
+                assert G.rel_err(got, refg) < G.FP32_TOL, (dtype, bwd_mode, k)
     X.close()
     torch.cuda.empty_cache()
