@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-loss-compare", action="store_true")
+    ap.add_argument("--nnz", type=float, default=None,
+                    help="run the workload's distributions and dims at this many entries "
+                         "(small cases for profiling; not a bench line)")
     ap.add_argument("--cpu-sample", type=int, default=12_000_000,
                     help="entries of the workload the CPU oracle runs on")
     return ap.parse_args()
@@ -132,27 +135,32 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-def kernel_source_hash() -> str:
+KERNEL_SOURCES = {"k_mttkrp": "mttkrp.cu", "k_loss_fwd": "cp_loss.cu", "k_loss_bwd": "cp_loss.cu"}
+
+
+def kernel_source_hash(kernel: str) -> str:
+    """Hash of the sources a kernel is built from (its .cu and the shared header)."""
     h = hashlib.sha256()
-    for f in ("mttkrp.cu", "pasta_internal.cuh"):
+    for f in (KERNEL_SOURCES[kernel], "pasta_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1902_03317_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
-    """DRAM bytes per MTTKRP launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", f"k_mttkrp_{workload}_traffic.txt")
+def profiled_traffic(kernel: str, workload: str):
+    """DRAM bytes (read + write) per launch of `kernel` from the committed ncu
+    summary profiles/<kernel>_<workload>_traffic.txt, if that capture was taken
+    on the current kernel source (else None)."""
+    p = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_traffic.txt")
     try:
         kv = {}
         for line in open(p):
             if ":" in line and not line.startswith("#"):
                 k, v = line.split(":", 1)
                 kv[k.strip()] = v.strip()
-        if kv.get("kernel_source_sha256_16") != kernel_source_hash():
+        if kv.get("kernel_source_sha256_16") != kernel_source_hash(kernel):
             return None
-        return float(kv["dram_bytes_per_launch_full_size"])
+        return float(kv["dram_bytes_per_launch_mean"])
     except Exception:
         return None
 
@@ -174,6 +182,8 @@ def run_own(args, rank, world, local):
         dist.init_process_group("gloo")
 
     wl = synth.WORKLOADS[args.workload]
+    if args.nnz:
+        wl = wl.scaled(nnz=int(args.nnz))
     N = wl.order
     # ---- inputs, resident in HBM
     Xd = synth.generate(wl, device=dev)
@@ -193,23 +203,29 @@ def run_own(args, rank, world, local):
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
+        # ev: 2N + 4 events: [mttkrp n start, end]*N, fwd start/end, bwd start/end
         for n in range(N):
             if ev is not None:
                 ev[2 * n].record(stream)
             pasta.mttkrp(X, Us, n, out=Ms[n])
             if ev is not None:
                 ev[2 * n + 1].record(stream)
-        pasta.cp_loss_fwd(X, Us, 0)
-        pasta.cp_loss_bwd(X, Us, -2)
         if ev is not None:
             ev[2 * N].record(stream)
+        pasta.cp_loss_fwd(X, Us, 0)
+        if ev is not None:
+            ev[2 * N + 1].record(stream)
+            ev[2 * N + 2].record(stream)
+        pasta.cp_loss_bwd(X, Us, -2)
+        if ev is not None:
+            ev[2 * N + 3].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * N + 1)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * N + 4)] for _ in range(args.steps)]
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -222,12 +238,12 @@ def run_own(args, rank, world, local):
     torch.cuda.synchronize()
     clk = clocks.stop()
     total_ms = start.elapsed_time(end)
-    mttkrp_ms = [[evs[k][2 * n].elapsed_time(evs[k][2 * n + 1]) for n in range(N)] for k in range(args.steps)]
-    loss_ms = [evs[k][2 * N - 1].elapsed_time(evs[k][2 * N]) for k in range(args.steps)]
-    sweep_ms = sum(sum(r) for r in mttkrp_ms) / args.steps
-    per_mode_ms = [sum(mttkrp_ms[k][n] for k in range(args.steps)) / args.steps for n in range(N)]
-    loss_ms_mean = sum(loss_ms) / args.steps
-    step_ms = total_ms / args.steps
+    K = args.steps
+    per_mode_ms = [sum(evs[k][2 * n].elapsed_time(evs[k][2 * n + 1]) for k in range(K)) / K for n in range(N)]
+    fwd_ms = sum(evs[k][2 * N].elapsed_time(evs[k][2 * N + 1]) for k in range(K)) / K
+    bwd_ms = sum(evs[k][2 * N + 2].elapsed_time(evs[k][2 * N + 3]) for k in range(K)) / K
+    sweep_ms = sum(per_mode_ms)
+    step_ms = total_ms / K
     if world > 1:
         t = torch.tensor([sweep_ms, step_ms], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -235,19 +251,30 @@ def run_own(args, rank, world, local):
 
     nnz = wl.nnz
     value = world * N * nnz / (sweep_ms * 1e-3)
-    # algorithmic bytes per launch (mode n): COO stream (N 32-bit indices + FP32
-    # value per entry) + touched rows of the other factors + the output write
+    # Algorithmic (compulsory) bytes, FP32 factors (s = 4): each pass over the
+    # COO stream reads N 32-bit indices and one FP32 value per entry; every
+    # factor row the pass needs is read once; each output row written once.
     es = 4
-    alg_bytes = [nnz * (4 * N + 4) + sum(touched[k] * wl.R * es for k in range(N) if k != n)
-                 + wl.dims[n] * wl.R * 4 for n in range(N)]
-    achieved = sum(alg_bytes) / (sweep_ms * 1e-3) / 1e9
+    coo = nnz * (4 * N + 4)
+    rows = [touched[k] * wl.R * es for k in range(N)]
+    out = [wl.dims[n] * wl.R * 4 for n in range(N)]
+    alg = {
+        "k_mttkrp": ([coo + sum(rows) - rows[n] + out[n] for n in range(N)], sweep_ms, N),
+        "k_loss_fwd": ([coo + sum(rows)], fwd_ms, 1),
+        "k_loss_bwd": ([coo + sum(rows) + out[n] for n in range(N)], bwd_ms, N),
+    }
     peak, peak_src = measured_peak_gbs()
-    traffic = profiled_traffic(args.workload)
-    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                "frac": round(achieved / peak, 4), "traffic": traffic,
-                "kernel": "k_mttkrp", "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
-                "alg_bytes_per_launch": alg_bytes,
-                "frac_vs_8TBs": round(achieved / 8000.0, 4)}
+    rooflines = {}
+    for kname, (bytes_per_launch, ms, launches) in alg.items():
+        achieved = sum(bytes_per_launch) / (ms * 1e-3) / 1e9
+        rooflines[kname] = {
+            "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kname, args.workload),
+            "kernel": kname, "launches_per_step": launches, "ms_per_step": round(ms, 4),
+            "alg_bytes_per_launch": bytes_per_launch,
+            "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
+            "frac_vs_8TBs": round(achieved / 8000.0, 4)}
+    dominant = max(rooflines, key=lambda k: rooflines[k]["ms_per_step"])
 
     result = {
         "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
@@ -256,9 +283,10 @@ def run_own(args, rank, world, local):
         "config": {"workload": workload_desc(wl), "step": "MTTKRP every mode + CP-loss fwd (mode-0 copy) + bwd (one pass per mode over its sorted copy)",
                    "l2": "no flush: inputs larger than L2 (COO stream 1.6 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
-        "roofline": roofline,
+        "roofline": rooflines[dominant],
+        "rooflines": rooflines,
         "breakdown_ms": {"mttkrp_per_mode": [round(x, 4) for x in per_mode_ms],
-                         "loss_fwd_bwd": round(loss_ms_mean, 4)},
+                         "loss_fwd": round(fwd_ms, 4), "loss_bwd": round(bwd_ms, 4)},
         "preprocess": {"sort_ms_per_mode": [round(x, 2) for x in t_sort]},
         "gpu_launches": args.steps * (N + 2 + N),
         "clocks": clk,
