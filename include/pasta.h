@@ -202,6 +202,49 @@ pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype 
                                int mode, const double *d_gscale, void *const *d_G, void *stream);
 
 /*
+ * pasta_cp_loss_fwd_noalloc -- the loss of pasta_cp_loss_fwd for callers that
+ * cannot allocate device memory.  The paper has no counterpart: this is a
+ * deployment variant of the same forward kernel.
+ *
+ * Who needs it: code that may not call cudaMalloc (or any allocating library
+ * routine) where it computes the loss -- work recorded into a stream capture
+ * owned by another framework, real-time or callback contexts, processes whose
+ * device memory belongs to a different allocator.  pasta_coo_create copies
+ * the tensor and keeps per-handle scratch, so it is not usable there; this
+ * call reads the caller's own arrays and keeps its scratch (the FP64 partial
+ * sums of the loss, one per thread block) in a fixed device array inside the
+ * library, so it allocates nothing and needs no handle.
+ *
+ *   order, dims, nnz  as for pasta_coo_create (limits as there)
+ *   d_idx             host array of order device pointers, uint32 indices in
+ *                     creation order; each array 16-byte aligned and readable
+ *                     up to nnz rounded up to a multiple of 4 entries (entries
+ *                     past nnz are read but ignored)
+ *   d_val             FP32 values, same alignment and readability rule
+ *   d_U, u_dtype, R, d_loss, d_resid   as for pasta_cp_loss_fwd with mode -1
+ * Indices are not validated: each must be < dims[k].
+ * Errors: PASTA_ERR_INVALID_ARG for sizes outside the library limits (order,
+ * dims, nnz, R) or NULL pointers, PASTA_ERR_ALIGNMENT for an input array that
+ * is not 16-byte aligned.
+ *
+ * The scratch array holds PASTA_NOALLOC_MAX_PARTIALS doubles (32 KB); every
+ * GPU that loads the library keeps it until the process exits.  Launches never
+ * use more thread blocks than it holds (the kernel strides over any nnz with
+ * that many blocks), and nothing in it has to start at zero.  All calls share
+ * it: calls whose work overlaps on the GPU (for example on two streams at
+ * once) race and give wrong losses; calls in sequence on one stream are safe.
+ * The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress, which may load the library's device code), so
+ * make the first call on each device before any stream capture.
+ */
+#define PASTA_NOALLOC_MAX_PARTIALS 4096
+
+pasta_status pasta_cp_loss_fwd_noalloc(int order, const uint64_t *dims, uint64_t nnz,
+                                       const uint32_t *const *d_idx, const float *d_val,
+                                       const void *const *d_U, pasta_dtype u_dtype, int R,
+                                       double *d_loss, void *d_resid, void *stream);
+
+/*
  * pasta_convert -- element-wise conversion of n values between pasta_dtypes
  * (round to nearest even on narrowing), e.g. FP32 gradient accumulators to
  * BF16 parameters.  Not a paper operation; it keeps the mixed-precision
