@@ -392,8 +392,8 @@ pasta_status pasta_cp_loss_fwd(pasta_coo X, const void *const *d_U, pasta_dtype 
         set_error("mode %d has no sorted copy", mode);
         return PASTA_ERR_NOT_SORTED;
     }
-    return launch_cp_loss_fwd(view_of(X, c), X->dims, X->num_sms, d_U, u_dtype, R, d_loss,
-                              d_resid, X->partials, X->partials_cap,
+    return launch_cp_loss_fwd(view_of(X, c), mode < 0 ? 0 : mode, X->num_sms, d_U, u_dtype, R,
+                              d_loss, d_resid, X->partials, X->partials_cap,
                               static_cast<cudaStream_t>(stream));
 }
 

@@ -319,6 +319,12 @@ __global__ void __launch_bounds__(kThreads) k_loss_bwd(const LossArgs<T, NM> a) 
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+template <typename T> constexpr pasta_dtype dtype_of();
+template <> constexpr pasta_dtype dtype_of<float>() { return PASTA_F32; }
+template <> constexpr pasta_dtype dtype_of<__nv_bfloat16>() { return PASTA_BF16; }
+template <> constexpr pasta_dtype dtype_of<__half>() { return PASTA_F16; }
+template <> constexpr pasta_dtype dtype_of<double>() { return PASTA_F64; }
+
 template <typename T, int NM>
 LossArgs<T, NM> make_args(const CooView &v, int rot, const void *const *U, void *const *G,
                           int R, const Geometry &g) {
@@ -385,6 +391,25 @@ pasta_status bwd_run(const pasta_coo_s *X, int seg_mode, const void *const *U, i
         const int mode = seg_mode == -2 ? p : seg_mode;
         const StoredCopy &c = mode < 0 ? X->orig : X->sorted[mode];
         const CooView v = view_of(X, c);
+        if (seg_mode == -2 && stream_supported(dtype_of<T>(), X->order, R, U, -1, G[mode])) {
+            StreamLaunch l;
+            l.order = X->order;
+            l.R = R;
+            l.dtype = dtype_of<T>();
+            for (int q = 0; q < X->order; ++q) {
+                const int k = (mode + q) % X->order;
+                l.idx[q] = v.idx[k];
+                l.U[q] = U[k];
+            }
+            l.val = v.val;
+            l.out = static_cast<float *>(G[mode]);
+            l.gscale = gscale;
+            l.nnz = v.nnz;
+            l.num_sms = X->num_sms;
+            pasta_status st = launch_stream(2, l, s);
+            if (st != PASTA_OK) return st;
+            continue;
+        }
         LossArgs<T, NM> a = make_args<T, NM>(v, mode < 0 ? 0 : mode, U, G, R, g);
         a.gscale = gscale;
         a.seg = mode >= 0 ? 1 : 0;
@@ -501,12 +526,35 @@ pasta_status convert_from(const S *src, void *dst, pasta_dtype dt, uint64_t n, c
 
 }  // namespace
 
-pasta_status launch_cp_loss_fwd(const CooView &v, const uint64_t *dims, int num_sms,
-                                const void *const *U, pasta_dtype dt, int R, double *loss,
-                                void *resid, double *partials, int cap, cudaStream_t s) {
-    (void)dims;
+pasta_status launch_cp_loss_fwd(const CooView &v, int rot, int num_sms, const void *const *U,
+                                pasta_dtype dt, int R, double *loss, void *resid,
+                                double *partials, int cap, cudaStream_t s) {
     if (v.nnz == 0) {
         PASTA_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s));
+        return PASTA_OK;
+    }
+    if (stream_supported(dt, v.order, R, U, -1, nullptr)) {
+        StreamLaunch l;
+        l.order = v.order;
+        l.R = R;
+        l.dtype = dt;
+        for (int p = 0; p < v.order; ++p) {
+            const int k = (rot + p) % v.order;
+            l.idx[p] = v.idx[k];
+            l.U[p] = U[k];
+        }
+        l.val = v.val;
+        l.out = static_cast<float *>(resid);
+        l.partials = partials;
+        l.nnz = v.nnz;
+        l.num_sms = num_sms;
+        l.max_blocks = cap;
+        int blocks = 0;
+        l.blocks_used = &blocks;
+        pasta_status st = launch_stream(1, l, s);
+        if (st != PASTA_OK) return st;
+        k_loss_finalize<<<1, 256, 0, s>>>(partials, blocks, loss);
+        PASTA_CUDA(cudaGetLastError());
         return PASTA_OK;
     }
     const bool fast = fast_path(dt, R, v.order, U, nullptr, resid);

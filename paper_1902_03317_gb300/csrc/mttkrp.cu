@@ -249,6 +249,24 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 pasta_status launch_mttkrp(const pasta_coo_s *X, const StoredCopy &c, const void *const *U,
                            pasta_dtype dt, int mode, int R, void *M, cudaStream_t s) {
+    if (stream_supported(dt, X->order, R, U, mode, M)) {
+        PASTA_CUDA(cudaMemsetAsync(M, 0, (size_t)X->dims[mode] * (size_t)R * sizeof(float), s));
+        if (X->nnz == 0) return PASTA_OK;
+        StreamLaunch l;
+        l.order = X->order;
+        l.R = R;
+        l.dtype = dt;
+        for (int p = 0; p < X->order; ++p) {
+            const int k = (mode + p) % X->order;
+            l.idx[p] = c.idx[k];
+            l.U[p] = U[k];
+        }
+        l.val = c.val;
+        l.out = static_cast<float *>(M);
+        l.nnz = X->nnz;
+        l.num_sms = X->num_sms;
+        return launch_stream(0, l, s);
+    }
     const int es = (int)dtype_size(dt);
     bool fast = ((R * es) % 16) == 0 && aligned16(M);
     for (int k = 0; k < X->order; ++k)

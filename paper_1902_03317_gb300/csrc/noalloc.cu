@@ -117,6 +117,6 @@ extern "C" pasta_status pasta_cp_loss_fwd_noalloc(int order, const uint64_t *dim
     v.order = order;
     // The launch never uses more blocks than the scratch holds (the grid is
     // capped at kNoallocPartials; the kernel's grid-stride loop covers any nnz).
-    return launch_cp_loss_fwd(v, dims, num_sms, d_U, u_dtype, R, d_loss, d_resid, partials,
+    return launch_cp_loss_fwd(v, 0, num_sms, d_U, u_dtype, R, d_loss, d_resid, partials,
                               kNoallocPartials, static_cast<cudaStream_t>(stream));
 }

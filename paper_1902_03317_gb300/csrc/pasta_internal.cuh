@@ -97,12 +97,35 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t stream);
 pasta_status launch_mttkrp(const pasta_coo_s *X, const StoredCopy &c, const void *const *U,
                            pasta_dtype dt, int mode, int R, void *M, cudaStream_t stream);
 
-// Loss forward over an arbitrary stored copy; `partials` must hold at least
+// Streaming kernels (stream.cu): one launch over a stored copy with the modes
+// rotated so that position 0 is the copy's sorted mode.
+struct StreamLaunch {
+    int order = 0;
+    int R = 0;
+    pasta_dtype dtype = PASTA_F32;
+    const uint32_t *idx[kMaxOrder] = {};  // by position
+    const void *U[kMaxOrder] = {};        // by position
+    const float *val = nullptr;
+    float *out = nullptr;           // MTTKRP: M; loss bwd: G of position 0; loss fwd: residuals or null
+    double *partials = nullptr;     // loss fwd
+    const double *gscale = nullptr; // loss bwd
+    uint64_t nnz = 0;
+    int num_sms = 0;
+    int max_blocks = 0;          // 0 = no cap
+    int *blocks_used = nullptr;  // optional
+};
+// True when the streaming kernels cover this case (see stream.cu).
+bool stream_supported(pasta_dtype dt, int order, int R, const void *const *U, int skip,
+                      const void *out);
+// kind: 0 MTTKRP, 1 loss forward, 2 loss backward (one mode)
+pasta_status launch_stream(int kind, const StreamLaunch &l, cudaStream_t s);
+
+// Loss forward over an arbitrary stored copy; `rot` is the copy's sorted mode
+// (0 for the creation-order copy); `partials` must hold at least
 // `partials_cap` doubles (the grid is capped to it).
-pasta_status launch_cp_loss_fwd(const CooView &v, const uint64_t *dims, int num_sms,
-                                const void *const *U, pasta_dtype dt, int R, double *loss,
-                                void *resid, double *partials, int partials_cap,
-                                cudaStream_t stream);
+pasta_status launch_cp_loss_fwd(const CooView &v, int rot, int num_sms, const void *const *U,
+                                pasta_dtype dt, int R, double *loss, void *resid,
+                                double *partials, int partials_cap, cudaStream_t stream);
 
 // seg_mode: >= 0 one pass over that sorted copy, -1 one pass over the
 // creation-order copy, -2 one pass per mode over each mode's sorted copy.

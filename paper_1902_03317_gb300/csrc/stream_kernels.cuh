@@ -1,0 +1,364 @@
+// Streaming kernels over a mode-sorted COO copy: MTTKRP (Eq. (mttkrp-init),
+// Algorithm 6), the CP-loss forward and the per-mode CP-loss backward share
+// one walk.
+//
+// Geometry: lanes span the rank (L lanes x 16 bytes cover a factor row, so
+// R * sizeof(T) == 16 L), G = 32/L lane groups per warp, each group owns a
+// contiguous "group tile" of the stream, and a block owns a contiguous "block
+// tile" made of its warps' group tiles in order.  COO words reach shared
+// memory by cp.async (one 16-byte copy per lane per array per 4 entries,
+// STAGES chunks in flight per warp); each batch of four entries is read back
+// with one 16-byte broadcast load per array, so no index shuffles are needed.
+// All factor-row loads of a batch are issued before any is used.
+//
+// Run reduction: the stream is sorted by position 0's mode, so the entries of
+// one output row are contiguous.  Each group keeps the running row sum in
+// registers.  A run that opens and closes inside its group tile is the whole
+// row: one plain 16-byte store per lane.  The first closed run of a group tile
+// and the run still open at its end go to shared-memory slots; after the
+// block tile, equal rows among the slots are summed and the combined run is
+// stored if it touches neither end of the block tile, else added with
+// red.global.add.  A row spanning many tiles thus costs one atomic per block
+// tile, which also keeps its FP32 rounding chain short.
+#pragma once
+
+#include "pasta_internal.cuh"
+
+namespace pasta {
+namespace stream {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+enum Kind : int { kMttkrp = 0, kLossFwd = 1, kLossBwd = 2 };
+
+template <typename T, int N>
+struct Args {
+    const uint32_t *idx[N];  // position p holds mode (rot + p) % N; position 0 is the sorted mode
+    const T *U[N];           // factor of position p (position 0 unused by MTTKRP)
+    const float *val;
+    float *out;              // MTTKRP: M; loss bwd: gradient of position 0; loss fwd: residuals or null
+    double *partials;        // loss fwd: per-block FP64 partial sums
+    const double *gscale;    // loss bwd: incoming gradient (null = 1)
+    uint64_t nnz;
+    uint32_t R;
+    int L, lshift;
+    int tile;  // entries per group tile, a multiple of 4L
+};
+
+__device__ __forceinline__ void cp_async16(uint32_t *smem, const void *gmem, int src_bytes) {
+    const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem),
+                 "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
+template <int K> __device__ __forceinline__ void cp_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(K));
+}
+
+// Shared memory per block: COO stages for every warp, then the combine slots
+// (one row index and R FP32 partials per slot, two slots per group).
+__host__ __device__ constexpr int coo_words_per_warp(int N, int stages, int L) {
+    return stages * (N + 1) * (32 / L) * (4 * L + 4);
+}
+__host__ __device__ constexpr int combine_slots(int L) { return 2 * kWarps * (32 / L); }
+__host__ __device__ constexpr size_t smem_bytes(int N, int stages, int L, int R) {
+    return (size_t)kWarps * coo_words_per_warp(N, stages, L) * 4 + (size_t)combine_slots(L) * 4 +
+           (size_t)combine_slots(L) * R * 4;
+}
+
+// Per-group running state.
+template <int VEC>
+struct GroupState {
+    float acc[VEC];
+    uint32_t cur;   // row of the open run (kNoRow before the first entry)
+    bool first;     // the open run began at the tile start
+    uint4 row0;     // loss kinds: position-0 factor row of the open run
+    double sq;      // loss fwd: this lane's FP64 sum of squared residuals
+};
+
+template <typename T, int N, int KIND>
+struct Ctx {
+    static constexpr int VEC = 16 / sizeof(T);
+    const Args<T, N> &a;
+    const char *ub[N];  // this lane's first byte of row 0 of every factor
+    uint32_t stride;    // bytes per factor row
+    int lane_off;       // this lane's first element of a row
+    int L, lig, gslot;
+    uint32_t *slot_row;
+    float *slot_val;
+    uint64_t t0;
+    float g_scale;
+};
+
+// Close the open run: the first closed run of a tile goes to slot 0, a later
+// one is a whole row and is stored.
+template <typename T, int N, int KIND>
+__device__ __forceinline__ void close_run(const Ctx<T, N, KIND> &c,
+                                          GroupState<Ctx<T, N, KIND>::VEC> &s) {
+    constexpr int VEC = Ctx<T, N, KIND>::VEC;
+    if (s.first) {
+        if (c.lig == 0) c.slot_row[2 * c.gslot] = s.cur;
+        float *d = c.slot_val + (size_t)(2 * c.gslot) * c.a.R + c.lane_off;
+#pragma unroll
+        for (int e = 0; e < VEC; e += 4)
+            *reinterpret_cast<float4 *>(d + e) = make_float4(s.acc[e], s.acc[e + 1], s.acc[e + 2], s.acc[e + 3]);
+    } else {
+        float *d = c.a.out + (uint64_t)s.cur * c.a.R + c.lane_off;
+#pragma unroll
+        for (int e = 0; e < VEC; e += 4) {
+            const float v4[4] = {s.acc[e], s.acc[e + 1], s.acc[e + 2], s.acc[e + 3]};
+            Store<float, 4>::run(d + e, v4);
+        }
+    }
+    s.first = false;
+}
+
+// One batch: the four entries held at position `src` of the group's chunk.
+// CHECK = false when all four are real entries (every full chunk).
+template <bool CHECK, typename T, int N, int KIND>
+__device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
+                                      GroupState<Ctx<T, N, KIND>::VEC> &s, const uint32_t *sb,
+                                      int AS, int src, int lim, uint64_t pos) {
+    constexpr int VEC = Ctx<T, N, KIND>::VEC;
+    constexpr int P0 = (KIND == kMttkrp) ? 1 : 0;  // first gathered position
+    constexpr int NR = N - P0;                     // rows gathered per entry
+    uint32_t iw[N][4];
+    float vw[4];
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const uint4 w = *reinterpret_cast<const uint4 *>(sb + k * AS + 4 * src);
+        iw[k][0] = w.x; iw[k][1] = w.y; iw[k][2] = w.z; iw[k][3] = w.w;
+    }
+    {
+        const float4 w = *reinterpret_cast<const float4 *>(sb + N * AS + 4 * src);
+        vw[0] = w.x; vw[1] = w.y; vw[2] = w.z; vw[3] = w.w;
+    }
+    // Phase A: all gathered rows of the four entries.  Position 0 (loss kinds)
+    // is loaded only where the run changes.
+    uint4 rows[4][NR];
+    bool need0[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool ok = !CHECK || q < lim;
+        need0[q] = ok && iw[0][q] != (q == 0 ? s.cur : iw[0][q - 1]);
+#pragma unroll
+        for (int p = P0; p < N; ++p) {
+            const uint4 *ptr = reinterpret_cast<const uint4 *>(c.ub[p] + (uint64_t)iw[p][q] * c.stride);
+            if (p == 0) {
+                if (need0[q]) rows[q][0] = __ldg(ptr);
+            } else if (CHECK) {
+                rows[q][p - P0] = ok ? __ldg(ptr) : make_uint4(0u, 0u, 0u, 0u);
+            } else {
+                rows[q][p - P0] = __ldg(ptr);
+            }
+        }
+    }
+    // Phase B
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool ok = !CHECK || q < lim;
+        const bool changed = ok && iw[0][q] != s.cur;
+        if (KIND != kLossFwd) {
+            if (__any_sync(kFull, changed)) {
+                if (changed) {
+                    if (s.cur != kNoRow) close_run(c, s);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) s.acc[e] = 0.f;
+                }
+            }
+        }
+        if (changed) s.cur = iw[0][q];
+        if (KIND != kMttkrp && need0[q]) s.row0 = rows[q][0];
+        float p[VEC], r[VEC];
+        if (KIND == kMttkrp) {
+            widen<T, VEC>(rows[q][0], r);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) p[e] = vw[q] * r[e];
+#pragma unroll
+            for (int k = 1; k < NR - 1; ++k) {
+                widen<T, VEC>(rows[q][k], r);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) p[e] *= r[e];
+            }
+            widen<T, VEC>(rows[q][NR - 1], r);
+            if (ok) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) s.acc[e] = fmaf(p[e], r[e], s.acc[e]);
+            }
+        } else {
+            // p = prod over positions 1..N-1; model = sum_r p * row0
+            widen<T, VEC>(rows[q][1], p);
+#pragma unroll
+            for (int k = 2; k < N; ++k) {
+                widen<T, VEC>(rows[q][k], r);
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) p[e] *= r[e];
+            }
+            widen<T, VEC>(s.row0, r);
+            float part = 0.f;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) part = fmaf(p[e], r[e], part);
+            for (int o = c.L >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o, c.L);
+            const float e_m = vw[q] - part;
+            if (KIND == kLossFwd) {
+                if (ok && c.lig == 0) {
+                    s.sq += (double)e_m * (double)e_m;
+                    if (c.a.out) c.a.out[pos + q] = e_m;
+                }
+            } else if (ok) {
+                const float w = -c.g_scale * e_m;
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) s.acc[e] = fmaf(w, p[e], s.acc[e]);
+            }
+        }
+    }
+}
+
+template <typename T, int N, int KIND, int STAGES, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
+    constexpr int VEC = 16 / sizeof(T);
+    extern __shared__ __align__(16) uint32_t smem[];
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int L = a.L;
+    const int lig = lane & (L - 1);
+    const int grp = lane >> a.lshift;
+    const int G = 32 >> a.lshift;
+    const int chunk = 4 * L;
+    const int GS = 4 * L + 4;  // padded words per group chunk (bank spread)
+    const int AS = G * GS;     // words per array per stage
+    const int SS = (N + 1) * AS;
+    uint32_t *wbuf = smem + (size_t)warp * STAGES * SS;
+    const int nchunks = a.tile / chunk;
+
+    Ctx<T, N, KIND> c{a};
+    c.stride = a.R * (uint32_t)sizeof(T);
+    c.lane_off = lig * VEC;
+#pragma unroll
+    for (int p = 0; p < N; ++p) c.ub[p] = reinterpret_cast<const char *>(a.U[p] + c.lane_off);
+    c.L = L;
+    c.lig = lig;
+    c.slot_row = smem + (size_t)kWarps * STAGES * SS;
+    c.slot_val = reinterpret_cast<float *>(c.slot_row + combine_slots(L));
+    c.g_scale = (KIND == kLossBwd && a.gscale) ? (float)*a.gscale : 1.f;
+
+    GroupState<VEC> s;
+    s.sq = 0.0;
+    s.row0 = make_uint4(0u, 0u, 0u, 0u);
+
+    const uint64_t block_span = (uint64_t)a.tile * (uint64_t)(G * kWarps);
+    const uint64_t nbt = (a.nnz + block_span - 1) / block_span;
+
+    for (uint64_t bt = blockIdx.x; bt < nbt; bt += gridDim.x) {
+        c.gslot = warp * G + grp;
+        c.t0 = bt * block_span + (uint64_t)c.gslot * (uint64_t)a.tile;
+        const uint64_t t0 = c.t0;
+        const int len = (int)(t0 < a.nnz ? min((uint64_t)a.tile, a.nnz - t0) : 0);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) s.acc[e] = 0.f;
+        s.cur = kNoRow;
+        s.first = true;
+        if (KIND != kLossFwd && lig == 0) {
+            c.slot_row[2 * c.gslot] = kNoRow;
+            c.slot_row[2 * c.gslot + 1] = kNoRow;
+        }
+
+        auto issue = [&](int ci, int stage) {
+            const int off = ci * chunk + 4 * lig;
+            const bool ld = ci < nchunks && off < len;
+            const uint64_t my = t0 + (uint64_t)off;
+            uint32_t *sb = wbuf + stage * SS + grp * GS + 4 * lig;
+#pragma unroll
+            for (int k = 0; k < N; ++k)
+                cp_async16(sb + k * AS, ld ? (const void *)(a.idx[k] + my) : (const void *)a.idx[k],
+                           ld ? 16 : 0);
+            cp_async16(sb + N * AS, ld ? (const void *)(a.val + my) : (const void *)a.val, ld ? 16 : 0);
+            cp_commit();
+        };
+#pragma unroll
+        for (int st = 0; st < STAGES - 1; ++st) issue(st, st);
+        for (int i = 0;; ++i) {
+            const int rem = len - i * chunk;
+            if (!__any_sync(kFull, i < nchunks && rem > 0)) break;
+            issue(i + STAGES - 1, (i + STAGES - 1) % STAGES);
+            cp_wait<STAGES - 1>();
+            __syncwarp();
+            const uint32_t *sb = wbuf + (i % STAGES) * SS + grp * GS;
+            const uint64_t pos = t0 + (uint64_t)(i * chunk);
+            if (__all_sync(kFull, rem >= chunk)) {
+                for (int src = 0; src < L; ++src)
+                    batch<false>(c, s, sb, AS, src, 4, pos + 4u * (uint64_t)src);
+            } else {
+                for (int src = 0; src < L; ++src)
+                    batch<true>(c, s, sb, AS, src, rem - 4 * src, pos + 4u * (uint64_t)src);
+            }
+            __syncwarp();
+        }
+        cp_wait<0>();
+        __syncwarp();
+
+        if (KIND != kLossFwd) {
+            // the run still open at the tile end -> slot 1
+            if (s.cur != kNoRow) {
+                if (lig == 0) c.slot_row[2 * c.gslot + 1] = s.cur;
+                float *d = c.slot_val + (size_t)(2 * c.gslot + 1) * a.R + c.lane_off;
+#pragma unroll
+                for (int e = 0; e < VEC; e += 4)
+                    *reinterpret_cast<float4 *>(d + e) =
+                        make_float4(s.acc[e], s.acc[e + 1], s.acc[e + 2], s.acc[e + 3]);
+            }
+            __syncthreads();
+            // Combine the block tile's slots.  Warp w takes candidate heads
+            // w, w + kWarps, ...; its lanes span the row.
+            const int nslots = combine_slots(L);
+            const uint32_t *sr = c.slot_row;
+            int first_valid = 0;
+            while (first_valid < nslots && sr[first_valid] == kNoRow) ++first_valid;
+            int last_valid = nslots - 1;
+            while (last_valid >= 0 && sr[last_valid] == kNoRow) --last_valid;
+            for (int h = warp; h < nslots; h += kWarps) {
+                const uint32_t row = sr[h];
+                if (row == kNoRow) continue;
+                int prev = h - 1;
+                while (prev >= 0 && sr[prev] == kNoRow) --prev;
+                if (prev >= 0 && sr[prev] == row) continue;  // not the first slot of its run
+                int end = h;
+                for (int u = h + 1; u < nslots; ++u) {
+                    if (sr[u] == kNoRow) continue;
+                    if (sr[u] != row) break;
+                    end = u;
+                }
+                const bool atomic = (h == first_valid) || (end == last_valid);
+                for (int t = lane; t < (int)a.R; t += 32) {
+                    float sum = 0.f;
+                    for (int u = h; u <= end; ++u)
+                        if (sr[u] == row) sum += c.slot_val[(size_t)u * a.R + t];
+                    float *d = a.out + (uint64_t)row * a.R + t;
+                    if (atomic)
+                        asm volatile("red.global.add.f32 [%0], %1;" ::"l"(d), "f"(sum));
+                    else
+                        *d = sum;
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    if (KIND == kLossFwd) {
+        double sq = s.sq;
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
+        __shared__ double ws[kWarps];
+        if (lane == 0) ws[warp] = sq;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < kWarps; ++w) t += ws[w];
+            a.partials[blockIdx.x] = t;
+        }
+    }
+}
+
+}  // namespace stream
+}  // namespace pasta
