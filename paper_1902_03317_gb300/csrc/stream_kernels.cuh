@@ -15,11 +15,13 @@
 // one output row are contiguous.  Each group keeps the running row sum in
 // registers.  A run that opens and closes inside its group tile is the whole
 // row: one plain 16-byte store per lane.  The first closed run of a group tile
-// and the run still open at its end go to shared-memory slots; after the
-// block tile, equal rows among the slots are summed and the combined run is
-// stored if it touches neither end of the block tile, else added with
-// red.global.add.  A row spanning many tiles thus costs one atomic per block
-// tile, which also keeps its FP32 rounding chain short.
+// (it may have begun in an earlier tile) is added with red.global.add.v4.f32;
+// the run still open at the tile end goes to a shared-memory slot, and after
+// the block tile equal rows among the slots are summed and added once.  A row
+// spanning many tiles thus costs one atomic per block tile, which also keeps
+// its FP32 rounding chain short.
+//
+// L2 policy: factor rows are re-read across the whole launch (evict-last).
 #pragma once
 
 #include "pasta_internal.cuh"
@@ -47,25 +49,46 @@ struct Args {
     int tile;  // entries per group tile, a multiple of 4L
 };
 
+// 16-byte asynchronous copy global -> shared, L1 bypassed; src_bytes < 16
+// fills the rest with zeros.  (The form with an L2 cache-policy operand
+// raised an illegal-instruction fault on GB300 together with src_bytes, so
+// the COO stream is copied without a policy.)
 __device__ __forceinline__ void cp_async16(uint32_t *smem, const void *gmem, int src_bytes) {
     const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem),
                  "r"(src_bytes));
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last() {
+    uint64_t p;
+    asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+// 16-byte read-only load of a factor row slice, kept in L2 preferentially.
+__device__ __forceinline__ uint4 ld_row(const uint4 *p, uint64_t pol) {
+    uint4 r;
+    asm("ld.global.nc.L2::cache_hint.v4.u32 {%0,%1,%2,%3}, [%4], %5;"
+        : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+        : "l"(p), "l"(pol));
+    return r;
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;"); }
 template <int K> __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(K));
 }
 
-// Shared memory per block: COO stages for every warp, then the combine slots
-// (one row index and R FP32 partials per slot, two slots per group).
+// Shared memory per block: the COO stages of every warp.  After a warp has
+// drained its stages at the end of a block tile, the same words hold its
+// groups' end-of-tile slots: G row indices (padded to 4 words), then G rows
+// of R FP32 partials (G * (R + 1) words <= the stage words for every covered
+// geometry).
 __host__ __device__ constexpr int coo_words_per_warp(int N, int stages, int L) {
     return stages * (N + 1) * (32 / L) * (4 * L + 4);
 }
-__host__ __device__ constexpr int combine_slots(int L) { return 2 * kWarps * (32 / L); }
 __host__ __device__ constexpr size_t smem_bytes(int N, int stages, int L, int R) {
-    return (size_t)kWarps * coo_words_per_warp(N, stages, L) * 4 + (size_t)combine_slots(L) * 4 +
-           (size_t)combine_slots(L) * R * 4;
+    (void)R;
+    return (size_t)kWarps * coo_words_per_warp(N, stages, L) * 4;
 }
 
 // Per-group running state.
@@ -75,7 +98,8 @@ struct GroupState {
     uint32_t cur;   // row of the open run (kNoRow before the first entry)
     bool first;     // the open run began at the tile start
     uint4 row0;     // loss kinds: position-0 factor row of the open run
-    double sq;      // loss fwd: this lane's FP64 sum of squared residuals
+    float sq32;     // loss fwd: FP32 sum of squared residuals of the current chunk
+    double sq;      // loss fwd: FP64 sum of the chunk sums
 };
 
 template <typename T, int N, int KIND>
@@ -86,31 +110,26 @@ struct Ctx {
     uint32_t stride;    // bytes per factor row
     int lane_off;       // this lane's first element of a row
     int L, lig, gslot;
-    uint32_t *slot_row;
-    float *slot_val;
     uint64_t t0;
+    uint64_t pol_rows;  // L2 evict-last policy for factor rows
     float g_scale;
 };
 
-// Close the open run: the first closed run of a tile goes to slot 0, a later
-// one is a whole row and is stored.
+// Close the open run: the first closed run of a tile may continue a run of an
+// earlier tile and is added atomically; a later one is a whole row and is
+// stored.
 template <typename T, int N, int KIND>
 __device__ __forceinline__ void close_run(const Ctx<T, N, KIND> &c,
                                           GroupState<Ctx<T, N, KIND>::VEC> &s) {
     constexpr int VEC = Ctx<T, N, KIND>::VEC;
-    if (s.first) {
-        if (c.lig == 0) c.slot_row[2 * c.gslot] = s.cur;
-        float *d = c.slot_val + (size_t)(2 * c.gslot) * c.a.R + c.lane_off;
+    float *d = c.a.out + (uint64_t)s.cur * c.a.R + c.lane_off;
 #pragma unroll
-        for (int e = 0; e < VEC; e += 4)
-            *reinterpret_cast<float4 *>(d + e) = make_float4(s.acc[e], s.acc[e + 1], s.acc[e + 2], s.acc[e + 3]);
-    } else {
-        float *d = c.a.out + (uint64_t)s.cur * c.a.R + c.lane_off;
-#pragma unroll
-        for (int e = 0; e < VEC; e += 4) {
-            const float v4[4] = {s.acc[e], s.acc[e + 1], s.acc[e + 2], s.acc[e + 3]};
-            Store<float, 4>::run(d + e, v4);
-        }
+    for (int e = 0; e < VEC; e += 4) {
+        const float v4[4] = {s.acc[e], s.acc[e + 1], s.acc[e + 2], s.acc[e + 3]};
+        if (s.first)
+            RedAdd<float, 4>::run(d + e, v4);  // may continue a run of an earlier tile
+        else
+            Store<float, 4>::run(d + e, v4);   // the whole row
     }
     s.first = false;
 }
@@ -147,11 +166,11 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
         for (int p = P0; p < N; ++p) {
             const uint4 *ptr = reinterpret_cast<const uint4 *>(c.ub[p] + (uint64_t)iw[p][q] * c.stride);
             if (p == 0) {
-                if (need0[q]) rows[q][0] = __ldg(ptr);
+                if (need0[q]) rows[q][0] = ld_row(ptr, c.pol_rows);
             } else if (CHECK) {
-                rows[q][p - P0] = ok ? __ldg(ptr) : make_uint4(0u, 0u, 0u, 0u);
+                rows[q][p - P0] = ok ? ld_row(ptr, c.pol_rows) : make_uint4(0u, 0u, 0u, 0u);
             } else {
-                rows[q][p - P0] = __ldg(ptr);
+                rows[q][p - P0] = ld_row(ptr, c.pol_rows);
             }
         }
     }
@@ -204,7 +223,10 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
             const float e_m = vw[q] - part;
             if (KIND == kLossFwd) {
                 if (ok && c.lig == 0) {
-                    s.sq += (double)e_m * (double)e_m;
+                    // FP32 within a chunk (at most 4L <= 128 positive terms,
+                    // relative error <= 127 u); FP64 across chunks.  GB300's
+                    // FP64 pipe is too narrow for one FP64 add per entry.
+                    s.sq32 = fmaf(e_m, e_m, s.sq32);
                     if (c.a.out) c.a.out[pos + q] = e_m;
                 }
             } else if (ok) {
@@ -240,12 +262,19 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
     for (int p = 0; p < N; ++p) c.ub[p] = reinterpret_cast<const char *>(a.U[p] + c.lane_off);
     c.L = L;
     c.lig = lig;
-    c.slot_row = smem + (size_t)kWarps * STAGES * SS;
-    c.slot_val = reinterpret_cast<float *>(c.slot_row + combine_slots(L));
+    c.pol_rows = policy_evict_last();
+    // end-of-tile slots (overlaid on each warp's drained COO stages)
+    const int G4 = (G + 3) & ~3;
+    auto slot_row = [&](int sidx) { return smem + (size_t)(sidx / G) * STAGES * SS + (sidx % G); };
+    auto slot_val = [&](int sidx) {
+        return reinterpret_cast<float *>(smem + (size_t)(sidx / G) * STAGES * SS + G4) +
+               (size_t)(sidx % G) * a.R;
+    };
     c.g_scale = (KIND == kLossBwd && a.gscale) ? (float)*a.gscale : 1.f;
 
     GroupState<VEC> s;
     s.sq = 0.0;
+    s.sq32 = 0.f;
     s.row0 = make_uint4(0u, 0u, 0u, 0u);
 
     const uint64_t block_span = (uint64_t)a.tile * (uint64_t)(G * kWarps);
@@ -260,10 +289,6 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
         for (int e = 0; e < VEC; ++e) s.acc[e] = 0.f;
         s.cur = kNoRow;
         s.first = true;
-        if (KIND != kLossFwd && lig == 0) {
-            c.slot_row[2 * c.gslot] = kNoRow;
-            c.slot_row[2 * c.gslot + 1] = kNoRow;
-        }
 
         auto issue = [&](int ci, int stage) {
             const int off = ci * chunk + 4 * lig;
@@ -294,52 +319,50 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
                 for (int src = 0; src < L; ++src)
                     batch<true>(c, s, sb, AS, src, rem - 4 * src, pos + 4u * (uint64_t)src);
             }
+            if (KIND == kLossFwd) {
+                s.sq += (double)s.sq32;
+                s.sq32 = 0.f;
+            }
             __syncwarp();
         }
         cp_wait<0>();
         __syncwarp();
 
         if (KIND != kLossFwd) {
-            // the run still open at the tile end -> slot 1
+            // The run still open at the tile end goes to this group's slot
+            // (the warp's stages are drained, so their words are free).
+            if (lig == 0) *slot_row(c.gslot) = s.cur;
             if (s.cur != kNoRow) {
-                if (lig == 0) c.slot_row[2 * c.gslot + 1] = s.cur;
-                float *d = c.slot_val + (size_t)(2 * c.gslot + 1) * a.R + c.lane_off;
+                float *d = slot_val(c.gslot) + c.lane_off;
 #pragma unroll
                 for (int e = 0; e < VEC; e += 4)
                     *reinterpret_cast<float4 *>(d + e) =
                         make_float4(s.acc[e], s.acc[e + 1], s.acc[e + 2], s.acc[e + 3]);
             }
             __syncthreads();
-            // Combine the block tile's slots.  Warp w takes candidate heads
-            // w, w + kWarps, ...; its lanes span the row.
-            const int nslots = combine_slots(L);
-            const uint32_t *sr = c.slot_row;
-            int first_valid = 0;
-            while (first_valid < nslots && sr[first_valid] == kNoRow) ++first_valid;
-            int last_valid = nslots - 1;
-            while (last_valid >= 0 && sr[last_valid] == kNoRow) --last_valid;
+            // Sum consecutive slots of equal row (in stream order) and add
+            // each sum once.  Warp w takes candidate heads w, w + kWarps, ...;
+            // its lanes span the row.
+            const int nslots = kWarps * G;
             for (int h = warp; h < nslots; h += kWarps) {
-                const uint32_t row = sr[h];
+                const uint32_t row = *slot_row(h);
                 if (row == kNoRow) continue;
                 int prev = h - 1;
-                while (prev >= 0 && sr[prev] == kNoRow) --prev;
-                if (prev >= 0 && sr[prev] == row) continue;  // not the first slot of its run
+                while (prev >= 0 && *slot_row(prev) == kNoRow) --prev;
+                if (prev >= 0 && *slot_row(prev) == row) continue;  // not the first slot of its run
                 int end = h;
                 for (int u = h + 1; u < nslots; ++u) {
-                    if (sr[u] == kNoRow) continue;
-                    if (sr[u] != row) break;
+                    const uint32_t ru = *slot_row(u);
+                    if (ru == kNoRow) continue;
+                    if (ru != row) break;
                     end = u;
                 }
-                const bool atomic = (h == first_valid) || (end == last_valid);
                 for (int t = lane; t < (int)a.R; t += 32) {
                     float sum = 0.f;
                     for (int u = h; u <= end; ++u)
-                        if (sr[u] == row) sum += c.slot_val[(size_t)u * a.R + t];
-                    float *d = a.out + (uint64_t)row * a.R + t;
-                    if (atomic)
-                        asm volatile("red.global.add.f32 [%0], %1;" ::"l"(d), "f"(sum));
-                    else
-                        *d = sum;
+                        if (*slot_row(u) == row) sum += slot_val(u)[t];
+                    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(a.out + (uint64_t)row * a.R + t),
+                                 "f"(sum));
                 }
             }
             __syncthreads();
