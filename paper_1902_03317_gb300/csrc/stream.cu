@@ -19,15 +19,15 @@ using stream::kWarps;
 
 constexpr int kStages = 2;
 
-// Blocks per SM each instantiation is compiled for: about the largest count
-// whose register budget (65536 / (256 * blocks)) holds the kernel without
-// spilling; MTTKRP gathers one row fewer per entry than the loss kernels.
+// Blocks per SM each instantiation is compiled for (register budget
+// 65536 / (256 * blocks)), chosen by measurement on the order-3 workloads:
+// occupancy outweighs a few spilled registers for MTTKRP and the forward,
+// not for the backward; higher orders need two blocks' budget.
 template <typename T, int N, int KIND>
 constexpr int min_blocks() {
     if (N != 3) return 2;
-    if (KIND == 0) return sizeof(T) == 4 ? 4 : 3;
-    if (KIND == 1) return 3;
-    return sizeof(T) == 4 ? 3 : 2;
+    if (KIND == 2) return 3;  // the backward spills too much at 4
+    return sizeof(T) == 4 ? 4 : 3;
 }
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }

@@ -141,8 +141,9 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
                                       GroupState<Ctx<T, N, KIND>::VEC> &s, const uint32_t *sb,
                                       int AS, int src, int lim, uint64_t pos) {
     constexpr int VEC = Ctx<T, N, KIND>::VEC;
-    constexpr int P0 = (KIND == kMttkrp) ? 1 : 0;  // first gathered position
-    constexpr int NR = N - P0;                     // rows gathered per entry
+    constexpr bool MT = (KIND == kMttkrp);
+    constexpr int P0 = MT ? 1 : 0;  // first gathered position
+    constexpr int NR = N - P0;      // rows gathered per entry
     uint32_t iw[N][4];
     float vw[4];
 #pragma unroll
@@ -167,6 +168,7 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
             const uint4 *ptr = reinterpret_cast<const uint4 *>(c.ub[p] + (uint64_t)iw[p][q] * c.stride);
             if (p == 0) {
                 if (need0[q]) rows[q][0] = ld_row(ptr, c.pol_rows);
+
             } else if (CHECK) {
                 rows[q][p - P0] = ok ? ld_row(ptr, c.pol_rows) : make_uint4(0u, 0u, 0u, 0u);
             } else {
@@ -189,7 +191,7 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
             }
         }
         if (changed) s.cur = iw[0][q];
-        if (KIND != kMttkrp && need0[q]) s.row0 = rows[q][0];
+        if (!MT && need0[q]) s.row0 = rows[q][0];
         float p[VEC], r[VEC];
         if (KIND == kMttkrp) {
             widen<T, VEC>(rows[q][0], r);
@@ -289,6 +291,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
         for (int e = 0; e < VEC; ++e) s.acc[e] = 0.f;
         s.cur = kNoRow;
         s.first = true;
+
 
         auto issue = [&](int ci, int stage) {
             const int off = ci * chunk + 4 * lig;
