@@ -7,8 +7,9 @@ values, R = 32 FP32 factors (synthetic, seeded; stands in for the paper's
 FROSTT-style tensors).
 
 One timed step = one pass of the hot path over the tensor: MTTKRP on every
-mode (each on its mode-sorted copy) followed by the CP-loss forward (over the
-mode-0 copy) and backward (one pass per mode over that mode's sorted copy).  The mode sorts are preprocessing: they run
+mode (each on its mode-sorted copy) followed by the CP loss and the gradient
+of every factor (pasta_cp_loss_fwd_bwd: one pass per mode over that mode's
+sorted copy, the first pass also summing the loss).  The mode sorts are preprocessing: they run
 once before timing, as the paper's "provided" sort does, and their time is
 reported under "preprocess".  `value` = N modes x nnz / (MTTKRP part of the
 step), summed over ranks, with device time taken by CUDA events on the
@@ -135,13 +136,21 @@ def measured_peak_gbs():
         return 6800.0, "fallback"
 
 
-KERNEL_SOURCES = {"k_mttkrp": "mttkrp.cu", "k_loss_fwd": "cp_loss.cu", "k_loss_bwd": "cp_loss.cu"}
+# Kernel groups of the step and the sources their kernels are built from.
+KERNEL_SOURCES = {
+    "mttkrp": ("stream_kernels.cuh", "stream.cu", "mttkrp.cu"),
+    "loss_fwd_bwd": ("stream_kernels.cuh", "stream.cu", "cp_loss.cu"),
+}
+KERNEL_NAMES = {
+    "mttkrp": "k_stream<T, N, 0, ...> (MTTKRP)",
+    "loss_fwd_bwd": "k_stream<T, N, 2, ...> (loss backward, first pass also sums the loss)",
+}
 
 
 def kernel_source_hash(kernel: str) -> str:
-    """Hash of the sources a kernel is built from (its .cu and the shared header)."""
+    """Hash of the sources a kernel group is built from (and the shared header)."""
     h = hashlib.sha256()
-    for f in (KERNEL_SOURCES[kernel], "pasta_internal.cuh"):
+    for f in (*KERNEL_SOURCES[kernel], "pasta_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1902_03317_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -203,7 +212,7 @@ def run_own(args, rank, world, local):
     stream = torch.cuda.current_stream()
 
     def step(ev=None):
-        # ev: 2N + 4 events: [mttkrp n start, end]*N, fwd start/end, bwd start/end
+        # ev: 2N + 2 events: [mttkrp n start, end]*N, loss fwd+bwd start/end
         for n in range(N):
             if ev is not None:
                 ev[2 * n].record(stream)
@@ -212,20 +221,16 @@ def run_own(args, rank, world, local):
                 ev[2 * n + 1].record(stream)
         if ev is not None:
             ev[2 * N].record(stream)
-        pasta.cp_loss_fwd(X, Us, 0)
+        pasta.cp_loss_fwd_bwd(X, Us)
         if ev is not None:
             ev[2 * N + 1].record(stream)
-            ev[2 * N + 2].record(stream)
-        pasta.cp_loss_bwd(X, Us, -2)
-        if ev is not None:
-            ev[2 * N + 3].record(stream)
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * N + 4)] for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(2 * N + 2)] for _ in range(args.steps)]
     start = torch.cuda.Event(enable_timing=True)
     end = torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -240,8 +245,7 @@ def run_own(args, rank, world, local):
     total_ms = start.elapsed_time(end)
     K = args.steps
     per_mode_ms = [sum(evs[k][2 * n].elapsed_time(evs[k][2 * n + 1]) for k in range(K)) / K for n in range(N)]
-    fwd_ms = sum(evs[k][2 * N].elapsed_time(evs[k][2 * N + 1]) for k in range(K)) / K
-    bwd_ms = sum(evs[k][2 * N + 2].elapsed_time(evs[k][2 * N + 3]) for k in range(K)) / K
+    loss_ms = sum(evs[k][2 * N].elapsed_time(evs[k][2 * N + 1]) for k in range(K)) / K
     sweep_ms = sum(per_mode_ms)
     step_ms = total_ms / K
     if world > 1:
@@ -259,9 +263,8 @@ def run_own(args, rank, world, local):
     rows = [touched[k] * wl.R * es for k in range(N)]
     out = [wl.dims[n] * wl.R * 4 for n in range(N)]
     alg = {
-        "k_mttkrp": ([coo + sum(rows) - rows[n] + out[n] for n in range(N)], sweep_ms, N),
-        "k_loss_fwd": ([coo + sum(rows)], fwd_ms, 1),
-        "k_loss_bwd": ([coo + sum(rows) + out[n] for n in range(N)], bwd_ms, N),
+        "mttkrp": ([coo + sum(rows) - rows[n] + out[n] for n in range(N)], sweep_ms, N),
+        "loss_fwd_bwd": ([coo + sum(rows) + out[n] for n in range(N)], loss_ms, N),
     }
     peak, peak_src = measured_peak_gbs()
     rooflines = {}
@@ -270,7 +273,8 @@ def run_own(args, rank, world, local):
         rooflines[kname] = {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kname, args.workload),
-            "kernel": kname, "launches_per_step": launches, "ms_per_step": round(ms, 4),
+            "kernel": KERNEL_NAMES[kname], "group": kname, "launches_per_step": launches,
+            "ms_per_step": round(ms, 4),
             "alg_bytes_per_launch": bytes_per_launch,
             "peak_source": f"{peak_src} hbm_gbs (MEASURED_PEAKS.json)",
             "frac_vs_8TBs": round(achieved / 8000.0, 4)}
@@ -280,15 +284,15 @@ def run_own(args, rank, world, local):
         "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc(wl), "step": "MTTKRP every mode + CP-loss fwd (mode-0 copy) + bwd (one pass per mode over its sorted copy)",
+        "config": {"workload": workload_desc(wl), "step": "MTTKRP every mode + CP loss and all gradients (one pass per mode over its sorted copy, the first also summing the loss)",
                    "l2": "no flush: inputs larger than L2 (COO stream 1.6 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
         "roofline": rooflines[dominant],
         "rooflines": rooflines,
         "breakdown_ms": {"mttkrp_per_mode": [round(x, 4) for x in per_mode_ms],
-                         "loss_fwd": round(fwd_ms, 4), "loss_bwd": round(bwd_ms, 4)},
+                         "loss_fwd_bwd": round(loss_ms, 4)},
         "preprocess": {"sort_ms_per_mode": [round(x, 2) for x in t_sort]},
-        "gpu_launches": args.steps * (N + 2 + N),
+        "gpu_launches": args.steps * (N + N + 1),
         "clocks": clk,
     }
     del Xd

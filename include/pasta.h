@@ -245,6 +245,23 @@ pasta_status pasta_cp_loss_fwd_noalloc(int order, const uint64_t *dims, uint64_t
                                        double *d_loss, void *d_resid, void *stream);
 
 /*
+ * pasta_cp_loss_fwd_bwd -- the loss of pasta_cp_loss_fwd and the gradients of
+ * g * loss (pasta_cp_loss_bwd with PASTA_BWD_PER_MODE) in N passes instead of
+ * N + 1: pass k streams the mode-k sorted copy and reduces G_k along runs,
+ * and the first pass also sums the squared residuals.  Every sorted copy must
+ * exist (else PASTA_ERR_NOT_SORTED).  For training steps that always need
+ * both; the loss is summed in a fixed order (reproducible bits for the same
+ * inputs and launch) but not necessarily in the same order as
+ * pasta_cp_loss_fwd, so the two may differ in the last bits.
+ *   d_loss    device FP64 scalar, overwritten
+ *   d_gscale  device FP64 scalar g (NULL means g = 1)
+ *   d_G       as for pasta_cp_loss_bwd
+ */
+pasta_status pasta_cp_loss_fwd_bwd(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype,
+                                   int R, double *d_loss, const double *d_gscale,
+                                   void *const *d_G, void *stream);
+
+/*
  * pasta_convert -- element-wise conversion of n values between pasta_dtypes
  * (round to nearest even on narrowing), e.g. FP32 gradient accumulators to
  * BF16 parameters.  Not a paper operation; it keeps the mixed-precision
@@ -252,6 +269,18 @@ pasta_status pasta_cp_loss_fwd_noalloc(int order, const uint64_t *dims, uint64_t
  */
 pasta_status pasta_convert(const void *d_src, pasta_dtype src_dtype, void *d_dst,
                            pasta_dtype dst_dtype, uint64_t n, void *stream);
+
+/*
+ * pasta_convert_scaled -- as pasta_convert, with dst = scale * src, where
+ * scale is the device FP64 scalar at d_scale (NULL means 1); e.g. applying
+ * the incoming gradient of a loss to gradients computed for g = 1.  The
+ * product is formed in FP32 for FP32/BF16/FP16 sources, in FP64 for FP64.
+ * In place (d_dst == d_src) only when both types are equal; otherwise the two
+ * buffers must not overlap.
+ */
+pasta_status pasta_convert_scaled(const void *d_src, pasta_dtype src_dtype, void *d_dst,
+                                  pasta_dtype dst_dtype, uint64_t n, const double *d_scale,
+                                  void *stream);
 
 #ifdef __cplusplus
 }

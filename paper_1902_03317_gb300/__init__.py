@@ -6,8 +6,8 @@ and a thin torch-facing API.  Nothing here computes on the CPU: if the
 library is missing, calls fail with a RuntimeError.
 """
 from .api import (CooTensor, CPLoss, acc_dtype, convert, cp_loss, cp_loss_bwd,  # noqa: F401
-                  cp_loss_fwd, mttkrp)
+                  cp_loss_fwd, cp_loss_fwd_bwd, mttkrp)
 from ._lib import PastaError  # noqa: F401
 
-__all__ = ["CooTensor", "CPLoss", "cp_loss", "cp_loss_fwd", "cp_loss_bwd", "mttkrp",
+__all__ = ["CooTensor", "CPLoss", "cp_loss", "cp_loss_fwd", "cp_loss_bwd", "cp_loss_fwd_bwd", "mttkrp",
            "convert", "acc_dtype", "PastaError"]

@@ -42,6 +42,8 @@ SIGNATURES = {
     "pasta_cp_loss_fwd": (_I, [_P, _P, _I, _I, _I, _P, _P, _P]),
     "pasta_cp_loss_bwd": (_I, [_P, _P, _I, _I, _I, _P, _P, _P]),
     "pasta_convert": (_I, [_P, _I, _P, _I, _U64, _P]),
+    "pasta_convert_scaled": (_I, [_P, _I, _P, _I, _U64, _P, _P]),
+    "pasta_cp_loss_fwd_bwd": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
     "pasta_cp_loss_fwd_noalloc": (_I, [_I, _P, _U64, _P, _P, _P, _I, _I, _P, _P, _P]),
 }
 

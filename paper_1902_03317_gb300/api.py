@@ -214,15 +214,45 @@ def cp_loss_bwd(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = BWD_PER_MO
     return G
 
 
-def convert(src: torch.Tensor, dtype: torch.dtype) -> torch.Tensor:
-    """Element-wise dtype conversion in libpasta (round to nearest even)."""
+def convert(src: torch.Tensor, dtype: torch.dtype, scale: torch.Tensor | None = None,
+            out: torch.Tensor | None = None) -> torch.Tensor:
+    """Element-wise ``(dtype)(scale * src)`` in libpasta (round to nearest
+    even); ``scale`` is an optional device scalar.  ``out`` may be ``src``
+    itself when the dtypes agree (in place)."""
     src = src.contiguous()
-    out = torch.empty(src.shape, dtype=dtype, device=src.device)
+    if out is None:
+        out = torch.empty(src.shape, dtype=dtype, device=src.device)
+    sp = None
+    if scale is not None:
+        scale = scale.to(device=src.device, dtype=torch.float64).reshape(()).contiguous()
+        sp = scale.data_ptr()
     with torch.cuda.device(src.device):
-        st = _lib.lib().pasta_convert(src.data_ptr(), pasta_dtype(src.dtype), out.data_ptr(),
-                                      pasta_dtype(dtype), src.numel(), _stream(src.device))
-    _lib.check(st, "pasta_convert")
+        st = _lib.lib().pasta_convert_scaled(src.data_ptr(), pasta_dtype(src.dtype), out.data_ptr(),
+                                             pasta_dtype(dtype), src.numel(), sp,
+                                             _stream(src.device))
+    _lib.check(st, "pasta_convert_scaled")
     return out
+
+
+def cp_loss_fwd_bwd(X: CooTensor, Us: Sequence[torch.Tensor],
+                    gscale: torch.Tensor | None = None):
+    """Loss and the gradients of ``gscale * loss`` in N passes (one per mode,
+    the first also summing the loss).  Returns (FP64 loss, list of FP32
+    gradients; FP64 for FP64 factors)."""
+    X.sort_all()
+    ptrs, dt, R = _factor_ptrs(X, Us)
+    loss = torch.empty((), dtype=torch.float64, device=X.device)
+    G = [torch.empty((d, R), dtype=acc_dtype(dt), device=X.device) for d in X.dims]
+    gp = None
+    if gscale is not None:
+        gscale = gscale.to(device=X.device, dtype=torch.float64).reshape(()).contiguous()
+        gp = gscale.data_ptr()
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_cp_loss_fwd_bwd(X.handle, ptrs, pasta_dtype(dt), R, loss.data_ptr(),
+                                              gp, _lib.ptr_array([g.data_ptr() for g in G]),
+                                              _stream(X.device))
+    _lib.check(st, "pasta_cp_loss_fwd_bwd")
+    return loss, G
 
 
 class CPLoss(torch.autograd.Function):
@@ -233,25 +263,38 @@ class CPLoss(torch.autograd.Function):
     are streamed: -1 creation order; n the mode-n sorted copy (the backward
     reduces mode n along runs, the others with atomics); -2 (default of
     ``cp_loss``) the forward over the mode-0 copy and the backward as one pass
-    per mode over each mode's sorted copy.  Returns an FP64 0-d tensor;
-    gradients come back in each factor's dtype (FP32 accumulation, converted
-    on the device)."""
+    per mode over each mode's sorted copy.  With -2 and any factor requiring a
+    gradient, the forward already computes the gradients for g = 1 in the
+    same N passes (pasta_cp_loss_fwd_bwd) and the backward only scales them
+    by the incoming gradient.  Returns an FP64 0-d tensor; gradients come back
+    in each factor's dtype (FP32 accumulation, converted on the device)."""
 
     @staticmethod
     def forward(ctx, X: CooTensor, mode: int, *Us: torch.Tensor):
         Us = [U.detach() for U in Us]
         ctx.X = X
         ctx.mode = mode
-        ctx.save_for_backward(*Us)
+        ctx.dtypes = [U.dtype for U in Us]
+        ctx.G = None
+        ctx.save_for_backward(*Us)  # a second backward (retain_graph) recomputes
+        if mode == BWD_PER_MODE and any(ctx.needs_input_grad[2:]):
+            loss, ctx.G = cp_loss_fwd_bwd(X, Us)
+            return loss
         return cp_loss_fwd(X, Us, 0 if mode == BWD_PER_MODE else mode)
 
     @staticmethod
     def backward(ctx, grad_out: torch.Tensor):
-        Us = ctx.saved_tensors
-        G = cp_loss_bwd(ctx.X, Us, ctx.mode, gscale=grad_out.detach().reshape(()))
+        g = grad_out.detach().reshape(())
         grads = []
-        for U, g in zip(Us, G):
-            grads.append(g if g.dtype == U.dtype else convert(g, U.dtype))
+        if ctx.G is not None:
+            for dt, G in zip(ctx.dtypes, ctx.G):
+                grads.append(convert(G, dt, scale=g, out=G if G.dtype == dt else None))
+            ctx.G = None
+        else:
+            Us = ctx.saved_tensors
+            mode = ctx.mode
+            for U, G in zip(Us, cp_loss_bwd(ctx.X, Us, mode, gscale=g)):
+                grads.append(G if G.dtype == U.dtype else convert(G, U.dtype))
         return (None, None, *grads)
 
 

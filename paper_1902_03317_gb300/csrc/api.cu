@@ -424,11 +424,45 @@ pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype 
 
 pasta_status pasta_convert(const void *d_src, pasta_dtype src_dtype, void *d_dst,
                            pasta_dtype dst_dtype, uint64_t n, void *stream) {
+    return pasta_convert_scaled(d_src, src_dtype, d_dst, dst_dtype, n, nullptr, stream);
+}
+
+pasta_status pasta_convert_scaled(const void *d_src, pasta_dtype src_dtype, void *d_dst,
+                                  pasta_dtype dst_dtype, uint64_t n, const double *d_scale,
+                                  void *stream) {
     if (!ok_dtype(src_dtype) || !ok_dtype(dst_dtype) || (n > 0 && (!d_src || !d_dst))) {
         set_error("bad dtype or NULL pointer");
         return PASTA_ERR_INVALID_ARG;
     }
-    return launch_convert(d_src, src_dtype, d_dst, dst_dtype, n, static_cast<cudaStream_t>(stream));
+    if (d_src == d_dst && src_dtype != dst_dtype) {
+        set_error("in-place conversion needs equal source and destination types");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    return launch_convert(d_src, src_dtype, d_dst, dst_dtype, n, d_scale,
+                          static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_cp_loss_fwd_bwd(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype,
+                                   int R, double *d_loss, const double *d_gscale,
+                                   void *const *d_G, void *stream) {
+    pasta_status st = check_factors(X, d_U, u_dtype, R, -1);
+    if (st != PASTA_OK) return st;
+    if (!d_loss || !d_G) {
+        set_error("d_loss or d_G is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < X->order; ++k) {
+        if (!d_G[k]) {
+            set_error("d_G[%d] is NULL", k);
+            return PASTA_ERR_INVALID_ARG;
+        }
+        if (!X->sorted[k].present) {
+            set_error("mode %d has no sorted copy", k);
+            return PASTA_ERR_NOT_SORTED;
+        }
+    }
+    return launch_cp_loss_fwd_bwd(X, d_U, u_dtype, R, d_loss, d_gscale, d_G,
+                                  static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -499,25 +499,35 @@ template <typename S> __device__ __forceinline__ float widen(S x);
 template <> __device__ __forceinline__ float widen<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
 template <> __device__ __forceinline__ float widen<__half>(__half x) { return __half2float(x); }
 
+// dst[i] = (D)(scale * src[i]) (scale = 1 when null), rounded to nearest
+// even; FP32 arithmetic except for FP64 sources.
 template <typename S, typename D>
-__global__ void k_convert(const S *src, D *dst, uint64_t n) {
+__global__ void k_convert(const S *src, D *dst, uint64_t n, const double *scale) {
+    const double sd = scale ? *scale : 1.0;
+    const float sf = (float)sd;
     for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (uint64_t)gridDim.x * blockDim.x) {
-        if constexpr (std::is_same<S, float>::value || std::is_same<S, double>::value)
-            dst[i] = cvt<S, D>(src[i]);
-        else
-            dst[i] = cvt<float, D>(widen<S>(src[i]));
+        if constexpr (std::is_same<S, double>::value) {
+            dst[i] = cvt<double, D>(scale ? sd * src[i] : src[i]);
+        } else {
+            float v;
+            if constexpr (std::is_same<S, float>::value)
+                v = src[i];
+            else
+                v = widen<S>(src[i]);
+            dst[i] = cvt<float, D>(scale ? sf * v : v);
+        }
     }
 }
 
 template <typename S>
 pasta_status convert_from(const S *src, void *dst, pasta_dtype dt, uint64_t n, cudaStream_t s,
-                          int blocks) {
+                          int blocks, const double *sc) {
     switch (dt) {
-        case PASTA_F32: k_convert<S, float><<<blocks, 256, 0, s>>>(src, (float *)dst, n); break;
-        case PASTA_BF16: k_convert<S, __nv_bfloat16><<<blocks, 256, 0, s>>>(src, (__nv_bfloat16 *)dst, n); break;
-        case PASTA_F16: k_convert<S, __half><<<blocks, 256, 0, s>>>(src, (__half *)dst, n); break;
-        case PASTA_F64: k_convert<S, double><<<blocks, 256, 0, s>>>(src, (double *)dst, n); break;
+        case PASTA_F32: k_convert<S, float><<<blocks, 256, 0, s>>>(src, (float *)dst, n, sc); break;
+        case PASTA_BF16: k_convert<S, __nv_bfloat16><<<blocks, 256, 0, s>>>(src, (__nv_bfloat16 *)dst, n, sc); break;
+        case PASTA_F16: k_convert<S, __half><<<blocks, 256, 0, s>>>(src, (__half *)dst, n, sc); break;
+        case PASTA_F64: k_convert<S, double><<<blocks, 256, 0, s>>>(src, (double *)dst, n, sc); break;
         default: return PASTA_ERR_INVALID_ARG;
     }
     PASTA_CUDA(cudaGetLastError());
@@ -573,15 +583,65 @@ pasta_status launch_cp_loss_bwd(const pasta_coo_s *X, int seg_mode, const void *
     return dispatch<BwdFn>(dt, fast, g.J, X->order, X, seg_mode, U, R, g, gscale, G, s);
 }
 
+pasta_status launch_cp_loss_fwd_bwd(const pasta_coo_s *X, const void *const *U, pasta_dtype dt,
+                                    int R, double *loss, const double *gscale, void *const *G,
+                                    cudaStream_t s) {
+    bool fast = stream_supported(dt, X->order, R, U, -1, nullptr);
+    for (int k = 0; k < X->order; ++k) fast = fast && aligned16(G[k]);
+    if (!fast) {
+        // general kernels: forward over the mode-0 copy, then one pass per mode
+        pasta_status st = launch_cp_loss_fwd(view_of(X, X->sorted[0]), 0, X->num_sms, U, dt, R,
+                                             loss, nullptr, X->partials, X->partials_cap, s);
+        if (st != PASTA_OK) return st;
+        return launch_cp_loss_bwd(X, -2, U, dt, R, gscale, G, s);
+    }
+    for (int k = 0; k < X->order; ++k)
+        PASTA_CUDA(cudaMemsetAsync(G[k], 0, (size_t)X->dims[k] * (size_t)R * sizeof(float), s));
+    if (X->nnz == 0) {
+        PASTA_CUDA(cudaMemsetAsync(loss, 0, sizeof(double), s));
+        return PASTA_OK;
+    }
+    for (int p = 0; p < X->order; ++p) {
+        const CooView v = view_of(X, X->sorted[p]);
+        StreamLaunch l;
+        l.order = X->order;
+        l.R = R;
+        l.dtype = dt;
+        for (int q = 0; q < X->order; ++q) {
+            const int k = (p + q) % X->order;
+            l.idx[q] = v.idx[k];
+            l.U[q] = U[k];
+        }
+        l.val = v.val;
+        l.out = static_cast<float *>(G[p]);
+        l.gscale = gscale;
+        l.nnz = v.nnz;
+        l.num_sms = X->num_sms;
+        int blocks = 0;
+        if (p == 0) {  // the first pass also sums the squared residuals
+            l.partials = X->partials;
+            l.max_blocks = X->partials_cap;
+            l.blocks_used = &blocks;
+        }
+        pasta_status st = launch_stream(2, l, s);
+        if (st != PASTA_OK) return st;
+        if (p == 0) {
+            k_loss_finalize<<<1, 256, 0, s>>>(X->partials, blocks, loss);
+            PASTA_CUDA(cudaGetLastError());
+        }
+    }
+    return PASTA_OK;
+}
+
 pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,
-                            uint64_t n, cudaStream_t s) {
+                            uint64_t n, const double *scale, cudaStream_t s) {
     if (n == 0) return PASTA_OK;
     const int blocks = (int)std::min<uint64_t>((n + 255) / 256, 4096);
     switch (st) {
-        case PASTA_F32: return convert_from<float>((const float *)src, dst, dt, n, s, blocks);
-        case PASTA_BF16: return convert_from<__nv_bfloat16>((const __nv_bfloat16 *)src, dst, dt, n, s, blocks);
-        case PASTA_F16: return convert_from<__half>((const __half *)src, dst, dt, n, s, blocks);
-        case PASTA_F64: return convert_from<double>((const double *)src, dst, dt, n, s, blocks);
+        case PASTA_F32: return convert_from<float>((const float *)src, dst, dt, n, s, blocks, scale);
+        case PASTA_BF16: return convert_from<__nv_bfloat16>((const __nv_bfloat16 *)src, dst, dt, n, s, blocks, scale);
+        case PASTA_F16: return convert_from<__half>((const __half *)src, dst, dt, n, s, blocks, scale);
+        case PASTA_F64: return convert_from<double>((const double *)src, dst, dt, n, s, blocks, scale);
     }
     return PASTA_ERR_INVALID_ARG;
 }

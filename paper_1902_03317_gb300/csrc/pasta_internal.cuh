@@ -133,8 +133,14 @@ pasta_status launch_cp_loss_bwd(const pasta_coo_s *X, int seg_mode, const void *
                                 pasta_dtype dt, int R, const double *gscale, void *const *G,
                                 cudaStream_t stream);
 
+// Loss and every factor's gradient (one pass per mode over its sorted copy;
+// the first pass also sums the loss).  All sorted copies must exist.
+pasta_status launch_cp_loss_fwd_bwd(const pasta_coo_s *X, const void *const *U, pasta_dtype dt,
+                                    int R, double *loss, const double *gscale, void *const *G,
+                                    cudaStream_t stream);
+
 pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,
-                            uint64_t n, cudaStream_t stream);
+                            uint64_t n, const double *scale, cudaStream_t stream);
 
 // ------------------------------------------------------ device primitives ---
 

@@ -41,7 +41,7 @@ struct Args {
     const T *U[N];           // factor of position p (position 0 unused by MTTKRP)
     const float *val;
     float *out;              // MTTKRP: M; loss bwd: gradient of position 0; loss fwd: residuals or null
-    double *partials;        // loss fwd: per-block FP64 partial sums
+    double *partials;        // loss fwd (and fused loss bwd, else null): per-block FP64 partial sums
     const double *gscale;    // loss bwd: incoming gradient (null = 1)
     uint64_t nnz;
     uint32_t R;
@@ -232,6 +232,9 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
                     if (c.a.out) c.a.out[pos + q] = e_m;
                 }
             } else if (ok) {
+                // fused forward: the backward pass over the first copy also
+                // sums the squared residuals (Args::partials set)
+                if (c.a.partials && c.lig == 0) s.sq32 = fmaf(e_m, e_m, s.sq32);
                 const float w = -c.g_scale * e_m;
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) s.acc[e] = fmaf(w, p[e], s.acc[e]);
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
                 for (int src = 0; src < L; ++src)
                     batch<true>(c, s, sb, AS, src, rem - 4 * src, pos + 4u * (uint64_t)src);
             }
-            if (KIND == kLossFwd) {
+            if (KIND == kLossFwd || (KIND == kLossBwd && a.partials)) {
                 s.sq += (double)s.sq32;
                 s.sq32 = 0.f;
             }
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
         }
     }
 
-    if (KIND == kLossFwd) {
+    if (KIND == kLossFwd || (KIND == kLossBwd && a.partials)) {
         double sq = s.sq;
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(kFull, sq, o);
         __shared__ double ws[kWarps];

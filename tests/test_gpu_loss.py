@@ -168,3 +168,57 @@ def test_convert_rounds_to_nearest_even():
         assert torch.equal(y, x.to(dt))
     z = pasta.convert(x.double(), torch.float32)
     assert torch.equal(z, x)
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("name,nnz,dims,R", [SHAPES[1], SHAPES[2], SHAPES[4]])
+def test_fused_loss_and_grad(name, nnz, dims, R, dtype):
+    """pasta_cp_loss_fwd_bwd: the loss and all gradients in N passes."""
+    Xh = G.synth.generate(G.small(name, nnz, dims))
+    idx, val = G.host(Xh)
+    _, dev, rounded = G.factors(dims, R, 13, dtype)
+    X = G.to_device(Xh)
+    loss, grads = pasta.cp_loss_fwd_bwd(X, dev, gscale=torch.tensor(0.5, dtype=torch.float64))
+    ref_loss = oracle.cp_loss(dims, idx, val, rounded)
+    assert abs(loss.item() - ref_loss) <= G.FP32_TOL * ref_loss
+    ref_G = oracle.cp_grad(dims, idx, val, rounded, g=0.5)
+    for k in range(len(dims)):
+        assert G.rel_err(grads[k].cpu().numpy(), ref_G[k]) < G.FP32_TOL, k
+    # reproducible bits
+    loss2, _ = pasta.cp_loss_fwd_bwd(X, dev, gscale=torch.tensor(0.5, dtype=torch.float64))
+    assert loss2.item() == loss.item()
+    X.close()
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_autograd_per_mode_uses_fused_pass_and_scales(dtype):
+    Xh = G.synth.generate(G.small("zipf3d", 60_000, (5_000, 3_000, 1_000)))
+    idx, val = G.host(Xh)
+    _, dev, rounded = G.factors(Xh.dims, 32, 14, dtype)
+    X = G.to_device(Xh)
+    params = [u.clone().requires_grad_(True) for u in dev]
+    loss = pasta.cp_loss(X, params)  # mode -2
+    (2.5 * loss).backward(retain_graph=True)
+    ref_G = oracle.cp_grad(Xh.dims, idx, val, rounded, g=2.5)
+    tol = G.FP32_TOL if dtype == torch.float32 else 4e-3  # BF16 rounding of the gradient
+    for p, r in zip(params, ref_G):
+        assert p.grad.dtype == dtype
+        assert G.rel_err(p.grad.float().cpu().numpy(), r) < tol
+    # a second backward recomputes instead of reusing the scaled gradients
+    for p in params:
+        p.grad = None
+    loss.backward()
+    ref_1 = oracle.cp_grad(Xh.dims, idx, val, rounded, g=1.0)
+    for p, r in zip(params, ref_1):
+        assert G.rel_err(p.grad.float().cpu().numpy(), r) < tol
+    X.close()
+
+
+def test_convert_scaled():
+    x = torch.randn(10_001, device=G.DEV)
+    sc = torch.tensor(-1.75, dtype=torch.float64, device=G.DEV)
+    assert torch.equal(pasta.convert(x, torch.float32, scale=sc), x * -1.75)
+    assert torch.equal(pasta.convert(x, torch.bfloat16, scale=sc), (x * -1.75).to(torch.bfloat16))
+    y = x.clone()
+    pasta.convert(y, torch.float32, scale=sc, out=y)
+    assert torch.equal(y, x * -1.75)
