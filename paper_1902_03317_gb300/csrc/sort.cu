@@ -5,8 +5,10 @@
 // The key of entry m is its coordinate in cyclic mode order starting at the
 // sorted mode, each mode taking ceil(log2(dims[k])) bits, cut to the leading
 // 64 bits.  A stable least-significant-digit radix sort (8-bit digits) of
-// (key, entry number) pairs gives the permutation; a gather then writes the
-// sorted SoA copy.  Equal keys keep creation order, so the result is unique.
+// (key, entry number) pairs gives the permutation; a final pass writes the
+// sorted SoA copy, decoding every index the key holds whole from the sorted
+// keys and gathering only the rest (and the values) through the permutation.
+// Equal keys keep creation order, so the result is unique.
 //
 // Radix pass = histogram per 4096-entry tile (digit-major table), exclusive
 // scan of each digit's row over tiles, stable scatter: inside a tile the
@@ -168,15 +170,26 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t *kin, const
 struct GatherDst {
     uint32_t *idx[kMaxOrder];
     float *val;
+    // Mode k whose index sits whole in the sorted key: decode it from the key
+    // (shift[k] >= 0, mask[k]); else (shift[k] < 0) gather it through perm.
+    int shift[kMaxOrder];
+    uint32_t mask[kMaxOrder];
 };
 
-__global__ void k_gather(CooView src, const uint32_t *perm, GatherDst dst) {
+// Writes the sorted copy: indices held whole by the key are decoded from the
+// sorted keys (coalesced), the rest and the values are gathered through the
+// permutation (one random 4-byte read each).
+__global__ void k_gather(CooView src, const uint32_t *perm, const uint64_t *keys, GatherDst dst) {
     for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < src.nnz;
          p += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t o = perm[p];
+        const uint64_t key = keys[p];
 #pragma unroll
-        for (int k = 0; k < kMaxOrder; ++k)
-            if (k < src.order) dst.idx[k][p] = src.idx[k][o];
+        for (int k = 0; k < kMaxOrder; ++k) {
+            if (k >= src.order) continue;
+            dst.idx[k][p] = dst.shift[k] >= 0 ? (uint32_t)(key >> dst.shift[k]) & dst.mask[k]
+                                              : src.idx[k][o];
+        }
         dst.val[p] = src.val[o];
     }
 }
@@ -248,9 +261,23 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
                                               vb[(p + 1) % 2], n, shift, ntiles, hist, totals);
     }
     GatherDst gd{};
-    for (int k = 0; k < X->order; ++k) gd.idx[k] = dst.idx[k];
+    for (int k = 0; k < X->order; ++k) {
+        gd.idx[k] = dst.idx[k];
+        gd.shift[k] = -1;
+    }
+    for (int p = 0; p < X->order; ++p) {
+        const int k = ks.mode[p];
+        const int b = bits_for(X->dims[k]);
+        if (b == 0) {  // a mode of size 1: every index is 0
+            gd.shift[k] = 0;
+            gd.mask[k] = 0u;
+        } else if (ks.use[p] && ks.shr[p] == 0) {  // held whole, right-aligned by final_shift
+            gd.shift[k] = ks.shl[p] - ks.final_shift;
+            gd.mask[k] = b >= 32 ? 0xFFFFFFFFu : ((1u << b) - 1u);
+        }
+    }
     gd.val = dst.val;
-    k_gather<<<gblocks, 256, 0, s>>>(src, dst.perm, gd);
+    k_gather<<<gblocks, 256, 0, s>>>(src, dst.perm, kb[passes % 2], gd);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) st = cuda_fail(le, "sort kernels");
     cudaFreeAsync(keys, s);
