@@ -97,7 +97,7 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t stream);
 pasta_status launch_mttkrp(const pasta_coo_s *X, const StoredCopy &c, const void *const *U,
                            pasta_dtype dt, int mode, int R, void *M, cudaStream_t stream);
 
-// Streaming kernels (stream.cu): one launch over a stored copy with the modes
+// Streaming kernels (stream.cu and its per-kind units): one launch over a stored copy with the modes
 // rotated so that position 0 is the copy's sorted mode.
 struct StreamLaunch {
     int order = 0;

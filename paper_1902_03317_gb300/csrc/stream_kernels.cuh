@@ -33,6 +33,8 @@ constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+__host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x / 2); }
+
 enum Kind : int { kMttkrp = 0, kLossFwd = 1, kLossBwd = 2 };
 
 template <typename T, int N>
@@ -243,22 +245,27 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
     }
 }
 
-template <typename T, int N, int KIND, int STAGES, int MINB>
+// LC: lanes per entry fixed at compile time (0 = read from Args), which turns
+// every lane-group stride, shared-memory offset and shuffle width into a
+// constant.
+template <typename T, int N, int KIND, int STAGES, int MINB, int LC = 0>
 __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
     constexpr int VEC = 16 / sizeof(T);
     extern __shared__ __align__(16) uint32_t smem[];
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
-    const int L = a.L;
+    const int L = LC ? LC : a.L;
+    const int lshift = LC ? ilog2(LC) : a.lshift;
     const int lig = lane & (L - 1);
-    const int grp = lane >> a.lshift;
-    const int G = 32 >> a.lshift;
+    const int grp = lane >> lshift;
+    const int G = 32 >> lshift;
+    const int tile = LC ? (4 * LC > 512 ? 4 * LC : 512) : a.tile;  // as make_geometry
     const int chunk = 4 * L;
     const int GS = 4 * L + 4;  // padded words per group chunk (bank spread)
     const int AS = G * GS;     // words per array per stage
     const int SS = (N + 1) * AS;
     uint32_t *wbuf = smem + (size_t)warp * STAGES * SS;
-    const int nchunks = a.tile / chunk;
+    const int nchunks = tile / chunk;
 
     Ctx<T, N, KIND> c{a};
     c.stride = a.R * (uint32_t)sizeof(T);
@@ -282,14 +289,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
     s.sq32 = 0.f;
     s.row0 = make_uint4(0u, 0u, 0u, 0u);
 
-    const uint64_t block_span = (uint64_t)a.tile * (uint64_t)(G * kWarps);
+    const uint64_t block_span = (uint64_t)tile * (uint64_t)(G * kWarps);
     const uint64_t nbt = (a.nnz + block_span - 1) / block_span;
 
     for (uint64_t bt = blockIdx.x; bt < nbt; bt += gridDim.x) {
         c.gslot = warp * G + grp;
-        c.t0 = bt * block_span + (uint64_t)c.gslot * (uint64_t)a.tile;
+        c.t0 = bt * block_span + (uint64_t)c.gslot * (uint64_t)tile;
         const uint64_t t0 = c.t0;
-        const int len = (int)(t0 < a.nnz ? min((uint64_t)a.tile, a.nnz - t0) : 0);
+        const int len = (int)(t0 < a.nnz ? min((uint64_t)tile, a.nnz - t0) : 0);
 #pragma unroll
         for (int e = 0; e < VEC; ++e) s.acc[e] = 0.f;
         s.cur = kNoRow;

@@ -1,0 +1,117 @@
+// Launch templates of the streaming kernels (stream_kernels.cuh), shared by
+// the three translation units that instantiate them: stream_mttkrp.cu (MTTKRP),
+// stream_loss_fwd.cu (CP-loss forward) and stream_loss_bwd.cu (per-mode
+// CP-loss backward).  One unit per kind keeps each compile short and lets the
+// build run them in parallel.
+#pragma once
+
+#include <algorithm>
+
+#include "stream_kernels.cuh"
+
+namespace pasta {
+namespace stream_launch {
+
+using stream::Args;
+using stream::k_stream;
+using stream::kThreads;
+using stream::kWarps;
+
+constexpr int kStages = 2;
+
+// Blocks per SM each instantiation is compiled for (register budget
+// 65536 / (256 * blocks)), chosen by measurement on the order-3 workloads:
+// occupancy outweighs a few spilled registers for MTTKRP and the forward,
+// not for the backward; higher orders need two blocks' budget.
+template <typename T, int N, int KIND>
+constexpr int min_blocks() {
+    if (N != 3) return 2;
+    if (KIND == stream::kLossBwd) return 3;  // the backward spills too much at 4
+    return sizeof(T) == 4 ? 4 : 3;
+}
+
+// LC > 0 compiles the lane count of a row in (LC must equal the geometry's
+// L); LC = 0 reads it from the arguments.
+template <typename T, int N, int KIND, int LC>
+pasta_status run(const StreamLaunch &l, cudaStream_t s) {
+    constexpr int MINB = min_blocks<T, N, KIND>();
+    Args<T, N> a{};
+    for (int p = 0; p < N; ++p) {
+        a.idx[p] = l.idx[p];
+        a.U[p] = static_cast<const T *>(l.U[p]);
+    }
+    a.val = l.val;
+    a.out = l.out;
+    a.partials = l.partials;
+    a.gscale = l.gscale;
+    a.nnz = l.nnz;
+    a.R = (uint32_t)l.R;
+    const Geometry g = make_geometry(l.R, 16 / (int)sizeof(T), (int)sizeof(T));
+    if (LC != 0 && g.L != LC) return PASTA_ERR_UNSUPPORTED;  // by_lanes picks LC = L
+    a.L = g.L;
+    a.lshift = g.lshift;
+    a.tile = g.tile;
+    const size_t smem = stream::smem_bytes(N, kStages, g.L, l.R);
+    auto kern = k_stream<T, N, KIND, kStages, MINB, LC>;
+    PASTA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    PASTA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
+    per_sm = std::max(per_sm, 1);
+    const uint64_t span = (uint64_t)g.tile * (uint64_t)(32 >> g.lshift) * kWarps;
+    const uint64_t nbt = std::max<uint64_t>(1, (l.nnz + span - 1) / span);
+    uint64_t blocks = std::min<uint64_t>(nbt, (uint64_t)l.num_sms * (uint64_t)per_sm);
+    if (l.max_blocks > 0) blocks = std::min<uint64_t>(blocks, (uint64_t)l.max_blocks);
+    kern<<<(int)blocks, kThreads, smem, s>>>(a);
+    PASTA_CUDA(cudaGetLastError());
+    if (l.blocks_used) *l.blocks_used = (int)blocks;
+    return PASTA_OK;
+}
+
+// The loss kinds get a compiled-in lane count for the common row widths
+// (32..256 bytes: R = 8..64 in FP32, 16..128 in 16-bit); it turns the lane
+// group's strides, shared-memory offsets and shuffle widths into constants,
+// which measured 4-6% faster for the backward.  MTTKRP gained nothing
+// measurable and keeps one instantiation per type and order.
+template <typename T, int N, int KIND>
+pasta_status by_lanes(const StreamLaunch &l, cudaStream_t s) {
+    if constexpr (KIND == stream::kMttkrp) {
+        return run<T, N, KIND, 0>(l, s);
+    } else {
+        switch (l.R * (int)sizeof(T) / 16) {
+            case 2: return run<T, N, KIND, 2>(l, s);
+            case 4: return run<T, N, KIND, 4>(l, s);
+            case 8: return run<T, N, KIND, 8>(l, s);
+            case 16: return run<T, N, KIND, 16>(l, s);
+            default: return run<T, N, KIND, 0>(l, s);
+        }
+    }
+}
+
+template <typename T, int KIND>
+pasta_status by_order(const StreamLaunch &l, cudaStream_t s) {
+    switch (l.order) {
+        case 3: return by_lanes<T, 3, KIND>(l, s);
+        case 4: return by_lanes<T, 4, KIND>(l, s);
+        case 5: return by_lanes<T, 5, KIND>(l, s);
+    }
+    return PASTA_ERR_UNSUPPORTED;
+}
+
+template <int KIND>
+pasta_status by_type(const StreamLaunch &l, cudaStream_t s) {
+    switch (l.dtype) {
+        case PASTA_F32: return by_order<float, KIND>(l, s);
+        case PASTA_BF16: return by_order<__nv_bfloat16, KIND>(l, s);
+        case PASTA_F16: return by_order<__half, KIND>(l, s);
+        default: return PASTA_ERR_UNSUPPORTED;
+    }
+}
+
+}  // namespace stream_launch
+
+// One per kind, each defined in its own translation unit.
+pasta_status launch_stream_mttkrp(const StreamLaunch &l, cudaStream_t s);
+pasta_status launch_stream_loss_fwd(const StreamLaunch &l, cudaStream_t s);
+pasta_status launch_stream_loss_bwd(const StreamLaunch &l, cudaStream_t s);
+
+}  // namespace pasta
