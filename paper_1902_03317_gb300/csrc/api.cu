@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 
 #include "pasta_internal.cuh"
@@ -27,6 +28,48 @@ void set_error(const char *fmt, ...) {
 pasta_status cuda_fail(cudaError_t e, const char *where) {
     set_error("%s: %s (%s)", where, cudaGetErrorName(e), cudaGetErrorString(e));
     return e == cudaErrorMemoryAllocation ? PASTA_ERR_NOMEM : PASTA_ERR_CUDA;
+}
+
+// Scratch memory (the sort's keys and histograms) comes from one
+// library-owned stream-ordered pool per device whose release threshold is
+// unbounded, so consecutive sorts reuse the mapped memory instead of mapping
+// it anew after every synchronisation.  pasta_coo_destroy trims the pools.
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaMallocAsync(p, bytes, s);
+    cudaMemPool_t pool;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        if (!g_pools[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            e = cudaMemPoolCreate(&g_pools[dev], &props);
+            if (e != cudaSuccess) {
+                g_pools[dev] = nullptr;
+                return e;
+            }
+            uint64_t keep = UINT64_MAX;
+            cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        pool = g_pools[dev];
+    }
+    return cudaMallocFromPoolAsync(p, bytes, pool, s);
+}
+
+void scratch_trim() {
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    for (int d = 0; d < kMaxDevices; ++d)
+        if (g_pools[d]) cudaMemPoolTrimTo(g_pools[d], 0);
 }
 
 size_t dtype_size(pasta_dtype t) {
@@ -259,6 +302,7 @@ pasta_status pasta_coo_destroy(pasta_coo X) {
     for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(X->sorted[k]);
     if (X->partials) cudaFree(X->partials);
     delete X;
+    scratch_trim();
     return PASTA_OK;
 }
 

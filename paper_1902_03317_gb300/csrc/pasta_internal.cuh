@@ -21,6 +21,10 @@ constexpr uint64_t kPadEntries = 1024;    // stored arrays are padded to this mu
 
 void set_error(const char *fmt, ...);
 pasta_status cuda_fail(cudaError_t e, const char *where);
+// Stream-ordered scratch from the library's per-device pool (release with
+// cudaFreeAsync); scratch_trim returns the pools' unused memory.
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+void scratch_trim();
 
 #define PASTA_CUDA(call)                                         \
     do {                                                         \

@@ -1,6 +1,6 @@
-// Mode-order sort of the COO stream (arXiv:1902.03317, Sec. 5.2.2: tensors
-// are sorted lexicographically "in the order of mode 1 > 2 > 3"; Sec. 2.3:
-// each iteration order wants its own sorted copy).
+// Mode-order sort of the COO stream (arXiv:1902.03317, Sec. 5.2.2: the
+// tensors are sorted lexicographically, the first mode most significant;
+// Sec. 2.3: each iteration order wants its own sorted copy).
 //
 // The key of entry m is its coordinate in cyclic mode order starting at the
 // sorted mode, each mode taking ceil(log2(dims[k])) bits, cut to the leading
@@ -11,9 +11,9 @@
 // Equal keys keep creation order, so the result is unique.
 //
 // Radix pass = histogram per 4096-entry tile (digit-major table), exclusive
-// scan of each digit's row over tiles, stable scatter: inside a tile the
-// entries are ranked round by round (256 at a time) with __match_any_sync
-// peer groups and per-warp digit counts, which keeps storage order.
+// scan of each digit's row over tiles, stable scatter: each warp ranks its
+// 512-entry sub-tile by digit in storage order, the tile is reordered by
+// digit in shared memory and written out in runs of equal digit.
 #include <algorithm>
 
 #include "pasta_internal.cuh"
@@ -51,23 +51,51 @@ __global__ void k_make_keys(CooView v, KeySpec ks, uint64_t *keys, uint32_t *per
     }
 }
 
+// A tile is kThreads x kItems entries; warp w of its block owns the
+// contiguous sub-tile [w * kWarpSpan, (w + 1) * kWarpSpan), read in rounds
+// of 32 consecutive entries.  Both radix kernels use this arrangement, so
+// every entry is loaded by one coalesced 8-byte access per lane.
+constexpr int kWarpsPerBlock = kThreads / 32;
+constexpr int kItems = kTile / kThreads;
+constexpr int kWarpSpan = 32 * kItems;
+constexpr int kBins = 256;
+static_assert(kWarpSpan <= 65536, "warp ranks are packed as 16-bit values");
+
+// Digit of a key for the pass at `shift`; entries past the end get a value
+// unique to their lane (>= kBins), so they match no real digit.
+__device__ __forceinline__ uint32_t digit_of(uint64_t key, int shift) {
+    return (uint32_t)(key >> shift) & (kBins - 1);
+}
+
 // hist[d * ntiles + tile] = number of entries of `tile` whose digit is d.
+// Plain shared atomics per entry (one sub-histogram per warp); measured
+// faster than aggregating equal digits with __match_any_sync first.
 __global__ void __launch_bounds__(kThreads) k_hist(const uint64_t *keys, uint64_t n, int shift,
                                                    uint32_t ntiles, uint32_t *hist) {
-    __shared__ uint32_t cnt[256];
-    cnt[threadIdx.x] = 0;
+    __shared__ uint32_t cnt[kWarpsPerBlock][kBins];
+    const int t = threadIdx.x;
+    const int lane = t & 31;
+    const int warp = t >> 5;
+#pragma unroll
+    for (int w = 0; w < kWarpsPerBlock; ++w) cnt[w][t] = 0;
     __syncthreads();
-    const uint64_t base = (uint64_t)blockIdx.x * kTile;
-    const int lane = threadIdx.x & 31;
-    for (int r = 0; r < kRounds; ++r) {
-        const uint64_t i = base + (uint64_t)r * kThreads + threadIdx.x;
-        const bool valid = i < n;
-        const uint32_t d = valid ? (uint32_t)((keys[i] >> shift) & 255u) : 0u;
-        const unsigned peers = __match_any_sync(FULL, valid ? d : 256u + lane);
-        if (valid && (peers & ((1u << lane) - 1u)) == 0) atomicAdd(&cnt[d], __popc(peers));
+    const uint64_t base = (uint64_t)blockIdx.x * kTile + (uint64_t)warp * kWarpSpan + lane;
+    const int64_t rem = (int64_t)n - (int64_t)base;  // entry j is real iff 32 j < rem
+    const uint64_t *kp = keys + base;
+    uint64_t k[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) k[j] = 32 * j < rem ? kp[32 * j] : 0ull;
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        const bool valid = 32 * j < rem;
+        const uint32_t d = digit_of(k[j], shift);
+        if (valid) atomicAdd(&cnt[warp][d], 1u);
     }
     __syncthreads();
-    hist[(uint64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+    uint32_t c = 0;
+#pragma unroll
+    for (int w = 0; w < kWarpsPerBlock; ++w) c += cnt[w][t];
+    hist[(uint64_t)t * ntiles + blockIdx.x] = c;
 }
 
 // Exclusive scan of row d (one block per digit) of the digit-major table;
@@ -109,61 +137,126 @@ __global__ void __launch_bounds__(1024) k_rowscan(uint32_t *hist, uint32_t ntile
     if (threadIdx.x == 0) totals[blockIdx.x] = carry;
 }
 
-__global__ void __launch_bounds__(kThreads) k_scatter(const uint64_t *kin, const uint32_t *vin,
-                                                      uint64_t *kout, uint32_t *vout, uint64_t n,
-                                                      int shift, uint32_t ntiles,
-                                                      const uint32_t *hist,
-                                                      const uint32_t *totals) {
-    __shared__ uint32_t s_base[256];
-    __shared__ uint32_t s_w[kThreads / 32][256];
+// Shared memory of k_scatter: the tile's keys and values in digit order.
+constexpr size_t kScatterSmem = (size_t)kTile * (sizeof(uint64_t) + sizeof(uint32_t));
+
+// Stable scatter of one tile.  (1) Each warp ranks its sub-tile round by
+// round: __match_any_sync finds the lanes of equal digit (measured faster
+// here than a shared-memory mask word per digit), the lowest of them reads
+// and advances the warp's running count of that digit, so an entry's warp
+// rank counts the equal digits before it in storage order.  (2) Per
+// digit, warp offsets and the tile-local start follow from those counts.
+// (3) The tile is reordered by digit in shared memory, and (4) written out in
+// that order: consecutive threads write consecutive positions of one digit's
+// output range, so the writes coalesce.
+__global__ void __launch_bounds__(kThreads, 2)
+    k_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout,
+              uint64_t n, int shift, uint32_t ntiles, const uint32_t *hist,
+              const uint32_t *totals) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    uint64_t *sk = reinterpret_cast<uint64_t *>(sm_raw);
+    uint32_t *sv = reinterpret_cast<uint32_t *>(sm_raw + (size_t)kTile * sizeof(uint64_t));
+    __shared__ uint32_t wcnt[kWarpsPerBlock][kBins];  // per-warp counts, then warp offsets
+    __shared__ uint32_t lstart[kBins];                // tile-local start of each digit
+    __shared__ uint32_t gbase[kBins];                 // output position of that start
+    __shared__ uint32_t wsum[kWarpsPerBlock];
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
-    // Digit bases: exclusive scan of the digit totals (256 entries).
+    const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+    for (int w = 0; w < kWarpsPerBlock; ++w) wcnt[w][t] = 0;
+
+    const uint64_t tbase = (uint64_t)blockIdx.x * kTile;
+    const int tlen = (int)min((uint64_t)kTile, n - tbase);
+    const uint64_t base = tbase + (uint64_t)warp * kWarpSpan + lane;
+    const int64_t rem = (int64_t)n - (int64_t)base;  // entry j is real iff 32 j < rem
+    const uint64_t *kp = kin + base;
+    const uint32_t *vp = vin + base;
+    uint64_t k[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) k[j] = 32 * j < rem ? kp[32 * j] : 0ull;
+    // Exclusive scan of the digit totals (digit base of this pass) plus this
+    // tile's scanned count: where the tile's first entry of digit t goes.
     {
-        uint32_t x = totals[t];
+        const uint32_t x = totals[t];
         uint32_t inc = x;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t y = __shfl_up_sync(FULL, inc, o);
             if (lane >= o) inc += y;
         }
-        if (lane == 31) s_w[0][warp] = inc;
-        __syncthreads();
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();  // also orders the wcnt zeroing before the ranking
         uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += s_w[0][w];
-        s_base[t] = before + inc - x + hist[(uint64_t)t * ntiles + blockIdx.x];
-        __syncthreads();
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        gbase[t] = before + inc - x + hist[(uint64_t)t * ntiles + blockIdx.x];
     }
-    const uint64_t base = (uint64_t)blockIdx.x * kTile;
-    for (int r = 0; r < kRounds; ++r) {
+    // (1) warp ranks (< kWarpSpan, two per register)
+    uint32_t r[kItems / 2];
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) s_w[w][t] = 0;
-        __syncthreads();
-        const uint64_t i = base + (uint64_t)r * kThreads + t;
-        const bool valid = i < n;
-        const uint64_t key = valid ? kin[i] : 0ull;
-        const uint32_t val = valid ? vin[i] : 0u;
-        const uint32_t d = (uint32_t)((key >> shift) & 255u);
-        const unsigned peers = __match_any_sync(FULL, valid ? d : 256u + lane);
-        const uint32_t below = __popc(peers & ((1u << lane) - 1u));
-        if (valid && below == 0) s_w[warp][d] = __popc(peers);
-        __syncthreads();
+    for (int j = 0; j < kItems; ++j) {
+        const bool valid = 32 * j < rem;
+        const uint32_t d = digit_of(k[j], shift);
+        const unsigned peers = __match_any_sync(FULL, valid ? d : kBins + lane);
+        const int leader = __ffs(peers) - 1;
+        uint32_t old = 0;
+        if (valid && lane == leader) {
+            old = wcnt[warp][d];
+            wcnt[warp][d] = old + __popc(peers);
+        }
+        const uint32_t rank = __shfl_sync(FULL, old, leader) + __popc(peers & lt);
+        if (j & 1)
+            r[j / 2] |= rank << 16;
+        else
+            r[j / 2] = rank;
+        __syncwarp();
+    }
+    // the values are loaded now, so the ranking holds fewer registers
+    uint32_t v[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) v[j] = 32 * j < rem ? vp[32 * j] : 0u;
+    __syncthreads();
+    // (2) warp offsets per digit, then the tile-local digit starts
+    {
         uint32_t run = 0;
 #pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) {
-            const uint32_t c = s_w[w][t];
-            s_w[w][t] = run;
+        for (int w = 0; w < kWarpsPerBlock; ++w) {
+            const uint32_t c = wcnt[w][t];
+            wcnt[w][t] = run;
             run += c;
         }
-        __syncthreads();
-        if (valid) {
-            const uint64_t pos = (uint64_t)s_base[d] + s_w[warp][d] + below;
-            kout[pos] = key;
-            vout[pos] = val;
+        uint32_t inc = run;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
         }
+        __syncthreads();  // wsum is reused
+        if (lane == 31) wsum[warp] = inc;
         __syncthreads();
-        s_base[t] += run;
-        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        lstart[t] = before + inc - run;
+    }
+    __syncthreads();
+    // (3) reorder the tile by digit in shared memory
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+        if (32 * j < rem) {
+            const uint32_t d = digit_of(k[j], shift);
+            const uint32_t lp = lstart[d] + wcnt[warp][d] + ((r[j / 2] >> (16 * (j & 1))) & 0xFFFFu);
+            sk[lp] = k[j];
+            sv[lp] = v[j];
+        }
+    }
+    __syncthreads();
+    // (4) coalesced write-out
+#pragma unroll 4
+    for (int q = t; q < tlen; q += kThreads) {
+        const uint64_t key = sk[q];
+        const uint32_t d = digit_of(key, shift);
+        const uint64_t gp = (uint64_t)gbase[d] + (uint32_t)(q - (int)lstart[d]);
+        kout[gp] = key;
+        vout[gp] = sv[q];
     }
 }
 
@@ -178,19 +271,46 @@ struct GatherDst {
 
 // Writes the sorted copy: indices held whole by the key are decoded from the
 // sorted keys (coalesced), the rest and the values are gathered through the
-// permutation (one random 4-byte read each).
-__global__ void k_gather(CooView src, const uint32_t *perm, const uint64_t *keys, GatherDst dst) {
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < src.nnz;
-         p += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t o = perm[p];
-        const uint64_t key = keys[p];
+// permutation (one random 4-byte read each).  Each thread takes kGatherItems
+// positions a grid stride apart and issues all their loads before any use,
+// so several random reads are in flight per thread.
+constexpr int kGatherItems = 4;
+
+__global__ void __launch_bounds__(256) k_gather(CooView src, const uint32_t *perm,
+                                                const uint64_t *keys, GatherDst dst) {
+    const uint64_t step = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t p0 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < src.nnz;
+         p0 += step * kGatherItems) {
+        uint32_t o[kGatherItems];
+        uint64_t key[kGatherItems];
+#pragma unroll
+        for (int j = 0; j < kGatherItems; ++j) {
+            const uint64_t p = p0 + (uint64_t)j * step;
+            o[j] = p < src.nnz ? perm[p] : 0u;
+            key[j] = p < src.nnz ? keys[p] : 0ull;
+        }
+        float v[kGatherItems];
+#pragma unroll
+        for (int j = 0; j < kGatherItems; ++j) v[j] = src.val[o[j]];
 #pragma unroll
         for (int k = 0; k < kMaxOrder; ++k) {
             if (k >= src.order) continue;
-            dst.idx[k][p] = dst.shift[k] >= 0 ? (uint32_t)(key >> dst.shift[k]) & dst.mask[k]
-                                              : src.idx[k][o];
+            uint32_t x[kGatherItems];
+#pragma unroll
+            for (int j = 0; j < kGatherItems; ++j)
+                x[j] = dst.shift[k] >= 0 ? (uint32_t)(key[j] >> dst.shift[k]) & dst.mask[k]
+                                         : src.idx[k][o[j]];
+#pragma unroll
+            for (int j = 0; j < kGatherItems; ++j) {
+                const uint64_t p = p0 + (uint64_t)j * step;
+                if (p < src.nnz) dst.idx[k][p] = x[j];
+            }
         }
-        dst.val[p] = src.val[o];
+#pragma unroll
+        for (int j = 0; j < kGatherItems; ++j) {
+            const uint64_t p = p0 + (uint64_t)j * step;
+            if (p < src.nnz) dst.val[p] = v[j];
+        }
     }
 }
 
@@ -233,14 +353,14 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
     uint64_t *keys = nullptr;
     uint32_t *tmpv = nullptr, *hist = nullptr;
     const size_t hist_n = (size_t)256 * ntiles + 256;
-    PASTA_CUDA(cudaMallocAsync((void **)&keys, 2 * n * sizeof(uint64_t), s));
-    cudaError_t e1 = cudaMallocAsync((void **)&tmpv, n * sizeof(uint32_t), s);
-    cudaError_t e2 = cudaMallocAsync((void **)&hist, hist_n * sizeof(uint32_t), s);
+    PASTA_CUDA(scratch_alloc((void **)&keys, 2 * n * sizeof(uint64_t), s));
+    cudaError_t e1 = scratch_alloc((void **)&tmpv, n * sizeof(uint32_t), s);
+    cudaError_t e2 = scratch_alloc((void **)&hist, hist_n * sizeof(uint32_t), s);
     if (e1 != cudaSuccess || e2 != cudaSuccess) {
         cudaFreeAsync(keys, s);
         if (tmpv) cudaFreeAsync(tmpv, s);
         if (hist) cudaFreeAsync(hist, s);
-        set_error("cudaMallocAsync of sort scratch failed");
+        set_error("allocation of sort scratch failed");
         return PASTA_ERR_NOMEM;
     }
     uint64_t *kb[2] = {keys, keys + n};
@@ -249,6 +369,8 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
     vb[1 - passes % 2] = tmpv;
     uint32_t *totals = hist + (size_t)256 * ntiles;
 
+    PASTA_CUDA(cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kScatterSmem));
     const CooView src = view_of(X, X->orig);
     const int gblocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16);
     pasta_status st = PASTA_OK;
@@ -257,7 +379,7 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
         const int shift = 8 * p;
         k_hist<<<ntiles, kThreads, 0, s>>>(kb[p % 2], n, shift, ntiles, hist);
         k_rowscan<<<256, 1024, 0, s>>>(hist, ntiles, totals);
-        k_scatter<<<ntiles, kThreads, 0, s>>>(kb[p % 2], vb[p % 2], kb[(p + 1) % 2],
+        k_scatter<<<ntiles, kThreads, kScatterSmem, s>>>(kb[p % 2], vb[p % 2], kb[(p + 1) % 2],
                                               vb[(p + 1) % 2], n, shift, ntiles, hist, totals);
     }
     GatherDst gd{};
