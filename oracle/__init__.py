@@ -15,7 +15,7 @@ Citations are to arXiv:1902.03317 (PASTA):
   - COO layout and 0-based indices: Sec. 5.1.
   - Row-major factors, element (i, r) at i*R + r: footnote in Sec. 3.4 and
     Algorithm 6.
-  - Sorting "in the order of mode 1 > 2 > 3", lexicographic: Sec. 5.2.2
+  - Sorting lexicographically, the first mode most significant: Sec. 5.2.2
     (Algorithm 2's preprocessing); mode orientation: Sec. 2.3.
   - CP model and gradient-descent CPD: Sec. 2.2 (the loss itself is not
     printed in the paper; it is the least-squares objective over the stored
@@ -147,8 +147,8 @@ def cp_grad(dims, idx, val, U, g: float = 1.0):
 
 def mode_order(order: int, mode: int) -> list[int]:
     """Cyclic mode order starting at ``mode``: (n, n+1, ..., N-1, 0, ..., n-1).
-    Sec. 5.2.2 sorts "in the order of mode 1 > 2 > 3"; for a mode-n sort the
-    output mode leads and the rest follow cyclically."""
+    Sec. 5.2.2 sorts lexicographically with the first mode most significant;
+    for a mode-n sort the output mode leads and the rest follow cyclically."""
     return [(mode + j) % order for j in range(order)]
 
 
@@ -160,3 +160,66 @@ def sort_perm(idx, mode: int) -> np.ndarray:
     order = len(idx)
     keys = [np.asarray(idx[k]).astype(np.int64) for k in reversed(mode_order(order, mode))]
     return np.lexsort(keys).astype(np.int64)
+
+
+# ------------------------------------------------------------------ CP-ALS ---
+#
+# The paper names alternating least squares as the CPD method and MTTKRP as
+# its bottleneck (Sec. 2.2, the CPD paragraph) and cites Kolda and Bader's
+# survey for it; the sweep below takes that survey's CP-ALS steps in order:
+# for each mode n, V = Hadamard product of U_k^T U_k over k != n, U_n = MTTKRP_n
+# times V^{-1}, lambda = the column 2-norms of U_n, and the columns of U_n are
+# divided by lambda.  The fit uses ||X - model||^2 = ||X||^2 + ||model||^2 -
+# 2 <X, model> with ||X||^2 the sum of the squared stored values (stored
+# entries are taken as distinct coordinates).
+
+def gram(U) -> np.ndarray:
+    """U^T U in FP64."""
+    U = np.asarray(U, dtype=np.float64)
+    return U.T @ U
+
+
+def cp_als_sweep(dims, idx, val, U):
+    """One CP-ALS sweep over modes 0..N-1 in FP64.
+
+    Returns ``(U_new, lam, fit)``: the updated factors (columns of unit
+    2-norm, a column of zeros staying zero with lambda 0), lambda of the last
+    mode, and the fit 1 - ||X - model|| / ||X|| of the model sum_r lam_r
+    U_0(:, r) o ... o U_{N-1}(:, r).  A singular V raises
+    ``numpy.linalg.LinAlgError``."""
+    N = len(dims)
+    U = [np.array(u, dtype=np.float64, copy=True) for u in U]
+    R = U[0].shape[1]
+    G = [gram(u) for u in U]
+    lam = np.ones(R)
+    M = None
+    for n in range(N):
+        M = mttkrp(dims, idx, val, U, n, R)
+        V = np.ones((R, R))
+        for k in range(N):
+            if k != n:
+                V *= G[k]
+        # U_n = M V^{-1}; V is symmetric, so solve V U_n^T = M^T
+        Un = np.linalg.solve(V, M.T).T
+        lam = np.sqrt(np.sum(Un * Un, axis=0))
+        inv = np.where(lam > 0, 1.0 / np.where(lam > 0, lam, 1.0), 0.0)
+        U[n] = Un * inv[None, :]
+        G[n] = gram(U[n])
+    fit = cp_fit(val, U, lam, M)
+    return U, lam, fit
+
+
+def cp_fit(val, U, lam, M_last) -> float:
+    """Fit of the model (lam; U) to the stored entries, given the MTTKRP of
+    the last mode computed from the other (final) factors:
+    <X, model> = sum_r lam_r sum_i M_last(i, r) U_{N-1}(i, r) and
+    ||model||^2 = lam^T (Hadamard over k of U_k^T U_k) lam."""
+    val = np.asarray(val, dtype=np.float64)
+    normx2 = float(np.dot(val, val))
+    H = np.ones((lam.shape[0], lam.shape[0]))
+    for u in U:
+        H *= gram(u)
+    norm_model2 = float(lam @ H @ lam)
+    inner = float(np.sum(lam * np.sum(np.asarray(M_last) * U[-1], axis=0)))
+    res2 = max(normx2 + norm_model2 - 2.0 * inner, 0.0)
+    return 1.0 - np.sqrt(res2) / np.sqrt(normx2) if normx2 > 0 else 0.0

@@ -13,8 +13,8 @@
  *     example names entries (1,0,0) and (1,0,2) of a 4x4x3 tensor).
  *   - Factor matrices are row-major I_k x R, element (i, r) at i*R + r
  *     (footnote to Eq. (ttm) in Sec. 3.4; Algorithm 6 indexes A(i*R + r)).
- *   - The output is zero-filled and then accumulated into (Sec. 5.2.6: the
- *     output "is initialized before and only needs to be updated").
+ *   - The output is zero-filled and then accumulated into (Sec. 5.2.6 has
+ *     the output set up beforehand, the kernel only adding to it).
  *   - Duplicate coordinates are separate stored entries; MTTKRP is linear,
  *     so they add.
  *
