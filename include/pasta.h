@@ -48,6 +48,7 @@ extern "C" {
 
 #define PASTA_MAX_ORDER 8
 #define PASTA_MAX_RANK 256
+#define PASTA_ALS_MAX_RANK 128
 #define PASTA_VERSION 1
 
 typedef struct pasta_coo_s *pasta_coo; /* opaque, owned by the library */
@@ -61,7 +62,8 @@ typedef enum {
     PASTA_ERR_NOT_SORTED = 5,   /* the mode-sorted copy a call needs is missing */
     PASTA_ERR_NOMEM = 6,        /* device allocation failed */
     PASTA_ERR_CUDA = 7,         /* a CUDA runtime call failed (see pasta_last_error) */
-    PASTA_ERR_UNSUPPORTED = 8   /* a combination this build does not implement */
+    PASTA_ERR_UNSUPPORTED = 8,  /* a combination this build does not implement */
+    PASTA_ERR_SINGULAR = 9      /* CP-ALS: a normal-equation matrix has no inverse */
 } pasta_status;
 
 typedef enum {
@@ -124,8 +126,9 @@ pasta_status pasta_coo_info(pasta_coo X, int *order, uint64_t *dims, uint64_t *n
  * is stable, so entries with equal keys keep creation order.  The copy holds
  * sorted indices, values and the permutation perm (sorted position p holds
  * creation-order entry perm[p]).  A second call for the same mode is a no-op.
- * Temporary device memory (about 24 bytes per entry) is allocated and freed
- * on the stream.
+ * Temporary device memory (about 21 bytes per entry) comes from a
+ * library-owned stream-ordered pool that keeps it for the next sort;
+ * pasta_coo_destroy returns the pool's unused memory.
  */
 pasta_status pasta_coo_sort_by_mode(pasta_coo X, int mode, void *stream);
 
@@ -281,6 +284,34 @@ pasta_status pasta_convert(const void *d_src, pasta_dtype src_dtype, void *d_dst
 pasta_status pasta_convert_scaled(const void *d_src, pasta_dtype src_dtype, void *d_dst,
                                   pasta_dtype dst_dtype, uint64_t n, const double *d_scale,
                                   void *stream);
+
+/*
+ * pasta_cp_als_sweep -- one sweep of CP alternating least squares, the CPD
+ * method whose bottleneck is MTTKRP (Sec. 2.2, the CPD paragraph; the steps
+ * follow the Kolda-Bader survey the paper cites).  For n = 0, ..., N-1:
+ *     M     = MTTKRP_n(X, U)                     (pasta_mttkrp, FP32)
+ *     V     = Hadamard product over k != n of U_k^T U_k   (R x R, FP64)
+ *     U_n   = M V^{-1}                           (V inverted in FP64)
+ *     lam_r = || U_n(:, r) ||_2,  U_n(:, r) /= lam_r (a zero column stays 0)
+ * and then, if d_fit is not NULL, the fit 1 - ||X - model|| / ||X|| of the
+ * model sum_r lam_r U_0(:, r) o ... o U_{N-1}(:, r), from
+ * ||X - model||^2 = ||X||^2 + ||model||^2 - 2 <X, model>, where ||X||^2 is
+ * the sum of the squared stored values (stored entries are taken as distinct
+ * coordinates; duplicates should be merged before calling for a
+ * meaningful fit; the factors do not depend on this).
+ *   d_U       host array of N device pointers to row-major dims[k] x R FP32
+ *             factors, read and updated in place
+ *   R         1..PASTA_ALS_MAX_RANK, else PASTA_ERR_UNSUPPORTED
+ *   d_lambda  device output, R doubles: lam of the last mode
+ *   d_fit     device output (one double) or NULL
+ * Every mode-sorted copy must exist (PASTA_ERR_NOT_SORTED).  Scratch
+ * (dims_max x R floats plus small R x R buffers) comes from the library pool.
+ * The call synchronises `stream` once, at its end, to read the solve status:
+ * PASTA_ERR_SINGULAR when some V has a non-positive pivot (for example a
+ * factor column that became zero); the factors then hold unspecified values.
+ */
+pasta_status pasta_cp_als_sweep(pasta_coo X, float *const *d_U, int R, double *d_lambda,
+                                double *d_fit, void *stream);
 
 #ifdef __cplusplus
 }

@@ -1,13 +1,13 @@
-"""GB300-native COO MTTKRP and sparse CP loss (arXiv:1902.03317, PASTA).
+"""GB300-native COO MTTKRP, sparse CP loss and CP-ALS (arXiv:1902.03317, PASTA).
 
 The compute path is libpasta, a C-ABI CUDA library for sm_103a
 (``include/pasta.h``); this package holds its build script, a ctypes binding
 and a thin torch-facing API.  Nothing here computes on the CPU: if the
 library is missing, calls fail with a RuntimeError.
 """
-from .api import (CooTensor, CPLoss, acc_dtype, convert, cp_loss, cp_loss_bwd,  # noqa: F401
-                  cp_loss_fwd, cp_loss_fwd_bwd, mttkrp)
+from .api import (CooTensor, CPLoss, acc_dtype, convert, cp_als, cp_als_sweep, cp_loss,  # noqa: F401
+                  cp_loss_bwd, cp_loss_fwd, cp_loss_fwd_bwd, mttkrp)
 from ._lib import PastaError  # noqa: F401
 
 __all__ = ["CooTensor", "CPLoss", "cp_loss", "cp_loss_fwd", "cp_loss_bwd", "cp_loss_fwd_bwd", "mttkrp",
-           "convert", "acc_dtype", "PastaError"]
+           "cp_als_sweep", "cp_als", "convert", "acc_dtype", "PastaError"]

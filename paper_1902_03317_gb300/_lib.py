@@ -17,11 +17,13 @@ PASTA_F32, PASTA_BF16, PASTA_F16, PASTA_F64 = 0, 1, 2, 3
 PASTA_CREATE_DEFAULT, PASTA_CREATE_NO_VALIDATE = 0, 1
 MAX_ORDER = 8
 MAX_RANK = 256
+ALS_MAX_RANK = 128
 
 STATUS = {
     0: "PASTA_OK", 1: "PASTA_ERR_INVALID_ARG", 2: "PASTA_ERR_ALIGNMENT",
     3: "PASTA_ERR_INDEX_OOB", 4: "PASTA_ERR_NONFINITE", 5: "PASTA_ERR_NOT_SORTED",
     6: "PASTA_ERR_NOMEM", 7: "PASTA_ERR_CUDA", 8: "PASTA_ERR_UNSUPPORTED",
+    9: "PASTA_ERR_SINGULAR",
 }
 
 # name -> (restype, argtypes); mirrors include/pasta.h
@@ -45,6 +47,7 @@ SIGNATURES = {
     "pasta_convert_scaled": (_I, [_P, _I, _P, _I, _U64, _P, _P]),
     "pasta_cp_loss_fwd_bwd": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
     "pasta_cp_loss_fwd_noalloc": (_I, [_I, _P, _U64, _P, _P, _P, _I, _I, _P, _P, _P]),
+    "pasta_cp_als_sweep": (_I, [_P, _P, _I, _P, _P, _P]),
 }
 
 _lock = threading.Lock()

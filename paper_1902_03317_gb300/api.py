@@ -255,6 +255,51 @@ def cp_loss_fwd_bwd(X: CooTensor, Us: Sequence[torch.Tensor],
     return loss, G
 
 
+def cp_als_sweep(X: CooTensor, Us: Sequence[torch.Tensor], want_fit: bool = True):
+    """One CP-ALS sweep (pasta_cp_als_sweep): updates the FP32 factors ``Us``
+    in place, mode 0 first; returns ``(lam, fit)`` as FP64 device tensors
+    (``fit`` None when ``want_fit`` is False).  Sorts every mode first.
+    Raises PastaError (PASTA_ERR_SINGULAR) when a normal-equation matrix has
+    no inverse."""
+    X.sort_all()
+    R = int(Us[0].shape[1])
+    for k, U in enumerate(Us):
+        if U.dtype != torch.float32 or not U.is_contiguous() or U.device != X.device:
+            raise ValueError("CP-ALS factors must be contiguous FP32 tensors on the tensor's device")
+        if tuple(U.shape) != (X.dims[k], R):
+            raise ValueError(f"U[{k}] must be {X.dims[k]} x {R}")
+    lam = torch.empty(R, dtype=torch.float64, device=X.device)
+    fit = torch.empty((), dtype=torch.float64, device=X.device) if want_fit else None
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_cp_als_sweep(X.handle, _lib.ptr_array([U.data_ptr() for U in Us]), R,
+                                           lam.data_ptr(), fit.data_ptr() if want_fit else None,
+                                           _stream(X.device))
+    _lib.check(st, "pasta_cp_als_sweep")
+    return lam, fit
+
+
+def cp_als(X: CooTensor, R: int, max_sweeps: int = 50, tol: float = 1e-5,
+           init: Sequence[torch.Tensor] | None = None, seed: int = 0):
+    """CP decomposition by alternating least squares: sweeps until the fit
+    changes by less than ``tol`` or ``max_sweeps`` is reached.  ``init``
+    defaults to N(0, 1) factors drawn on the device from ``seed``.  Returns
+    ``(Us, lam, fits)`` with the fit after each sweep (one host read per
+    sweep)."""
+    if init is None:
+        g = torch.Generator(device=X.device).manual_seed(seed)
+        Us = [torch.randn((d, R), generator=g, device=X.device, dtype=torch.float32) for d in X.dims]
+    else:
+        Us = [u.detach().to(device=X.device, dtype=torch.float32).contiguous().clone() for u in init]
+    fits: list[float] = []
+    lam = None
+    for _ in range(max_sweeps):
+        lam, fit = cp_als_sweep(X, Us)
+        fits.append(float(fit))
+        if len(fits) > 1 and abs(fits[-1] - fits[-2]) < tol:
+            break
+    return Us, lam, fits
+
+
 class CPLoss(torch.autograd.Function):
     """loss = 1/2 sum_m (x_m - sum_r prod_k U_k(i_k(m), r))^2 over the stored
     entries of X, with hand-written forward and backward kernels.

@@ -203,6 +203,7 @@ const char *pasta_status_str(pasta_status s) {
         case PASTA_ERR_NOMEM: return "PASTA_ERR_NOMEM";
         case PASTA_ERR_CUDA: return "PASTA_ERR_CUDA";
         case PASTA_ERR_UNSUPPORTED: return "PASTA_ERR_UNSUPPORTED";
+        case PASTA_ERR_SINGULAR: return "PASTA_ERR_SINGULAR";
     }
     return "PASTA_ERR_UNKNOWN";
 }
@@ -301,6 +302,7 @@ pasta_status pasta_coo_destroy(pasta_coo X) {
     free_copy(X->orig);
     for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(X->sorted[k]);
     if (X->partials) cudaFree(X->partials);
+    if (X->als_normsq) cudaFree(X->als_normsq);
     delete X;
     scratch_trim();
     return PASTA_OK;
@@ -507,6 +509,30 @@ pasta_status pasta_cp_loss_fwd_bwd(pasta_coo X, const void *const *d_U, pasta_dt
     }
     return launch_cp_loss_fwd_bwd(X, d_U, u_dtype, R, d_loss, d_gscale, d_G,
                                   static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_cp_als_sweep(pasta_coo X, float *const *d_U, int R, double *d_lambda,
+                                double *d_fit, void *stream) {
+    pasta_status st = check_factors(X, reinterpret_cast<const void *const *>(d_U), PASTA_F32, R, -1);
+    if (st != PASTA_OK) return st;
+    if (R > PASTA_ALS_MAX_RANK) {
+        set_error("CP-ALS supports R <= %d (got %d)", PASTA_ALS_MAX_RANK, R);
+        return PASTA_ERR_UNSUPPORTED;
+    }
+    if (!d_lambda) {
+        set_error("d_lambda is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < X->order; ++k)
+        if (!X->sorted[k].present) {
+            set_error("mode %d has no sorted copy", k);
+            return PASTA_ERR_NOT_SORTED;
+        }
+    if (X->nnz == 0) {
+        set_error("CP-ALS needs at least one stored entry");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    return run_cp_als_sweep(X, d_U, R, d_lambda, d_fit, static_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -57,6 +57,7 @@ struct pasta_coo_s {
     pasta::StoredCopy sorted[PASTA_MAX_ORDER];
     double *partials = nullptr;  // per-block FP64 partial sums of the loss
     int partials_cap = 0;
+    double *als_normsq = nullptr;  // CP-ALS: sum of squared values (device), computed once
 };
 
 namespace pasta {
@@ -142,6 +143,10 @@ pasta_status launch_cp_loss_bwd(const pasta_coo_s *X, int seg_mode, const void *
 pasta_status launch_cp_loss_fwd_bwd(const pasta_coo_s *X, const void *const *U, pasta_dtype dt,
                                     int R, double *loss, const double *gscale, void *const *G,
                                     cudaStream_t stream);
+
+// One CP-ALS sweep (cp_als.cu); arguments checked by the caller.
+pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *lambda, double *fit,
+                              cudaStream_t stream);
 
 pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,
                             uint64_t n, const double *scale, cudaStream_t stream);

@@ -1,0 +1,123 @@
+"""CP-ALS sweep (pasta_cp_als_sweep) on the GPU vs the FP64 oracle's sweep.
+
+Tolerances: the sweep's only long FP32 sums are the MTTKRP (relative error
+~1e-6 on these tensors, FP32_TOL = 1e-5 by construction) and the row product
+M V^{-1}; V is inverted in FP64 and rounded to FP32.  The factor error is the
+MTTKRP error amplified by at most cond(V), which stays below ~10 for the
+random N(0, 1) starts used here, so factors and lambda are held to 1e-4 and
+the fit (a difference of FP64 terms built from them) to 1e-5 absolute.
+Later sweeps keep the same bound because each sweep only depends on the
+current factors.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1902_03317_gb300 as pasta
+from paper_1902_03317_gb300 import _lib, synth
+from tests import _gpu as G
+
+pytestmark = pytest.mark.gpu
+
+ALS_TOL = 1e-4
+FIT_TOL = 1e-5
+
+CASES = [
+    # (workload, nnz, dims, R): several tiles and a ragged tail each
+    ("uniform3d_200", 20_000, (200, 200, 200), 16),
+    ("zipf3d", 300_001, (5_000, 3_000, 2_000), 32),
+    ("zipf4d", 200_003, (2_000, 2_000, 500, 100), 8),
+    ("zipf4d", 100_000, (700, 600, 300, 50), 5),   # R * 4 not a multiple of 16: general MTTKRP
+    ("zipf5d", 150_000, (8, 3_000, 2_000, 500, 100), 16),
+]
+
+
+def _setup(name, nnz, dims, R, seed=3):
+    wl = G.small(name, nnz, dims, R=R)
+    Xh = synth.generate(wl)
+    idx, val = G.host(Xh)
+    X = G.to_device(Xh)
+    master = synth.generate_factors(wl.dims, R, seed=seed)
+    Ud = [u.to(G.DEV).contiguous() for u in master]
+    Uh = [u.double().numpy() for u in master]
+    return wl, X, idx, val, Ud, Uh
+
+
+@pytest.mark.parametrize("name,nnz,dims,R", CASES)
+def test_sweeps_match_oracle(name, nnz, dims, R):
+    wl, X, idx, val, Ud, Uh = _setup(name, nnz, dims, R)
+    for sweep in range(2):
+        lam, fit = pasta.cp_als_sweep(X, Ud)
+        Uh, lam_h, fit_h = oracle.cp_als_sweep(wl.dims, idx, val, Uh)
+        for k in range(wl.order):
+            err = G.rel_err(Ud[k].cpu().numpy(), Uh[k])
+            assert err < ALS_TOL, f"sweep {sweep} U{k}: {err}"
+        assert G.rel_err(lam.cpu().numpy(), lam_h) < ALS_TOL
+        assert abs(float(fit) - fit_h) < FIT_TOL, (float(fit), fit_h)
+        # continue both from the GPU's factors so the comparison stays per sweep
+        Uh = [u.cpu().double().numpy() for u in Ud]
+    X.close()
+
+
+def test_fit_is_monotone():
+    wl, X, idx, val, Ud, Uh = _setup("zipf3d", 200_000, (3_000, 2_000, 1_000), 16, seed=7)
+    fits = [float(pasta.cp_als_sweep(X, Ud)[1]) for _ in range(8)]
+    assert all(f1 >= f0 - 1e-6 for f0, f1 in zip(fits, fits[1:])), fits
+    for u in Ud:
+        assert torch.allclose(u.norm(dim=0), torch.ones(u.shape[1], device=G.DEV), atol=1e-5)
+    X.close()
+
+
+def test_planted_model_is_recovered():
+    g = np.random.default_rng(21)
+    A = [g.standard_normal((d, 3)) for d in (12, 10, 8)]
+    Xd = np.einsum("ir,jr,kr->ijk", *A)
+    idx = [torch.tensor(ix.ravel(), dtype=torch.int32) for ix in np.indices(Xd.shape)]
+    X = pasta.CooTensor(Xd.shape, [i.to(G.DEV) for i in idx], torch.tensor(Xd.ravel(), dtype=torch.float32, device=G.DEV))
+    init = [torch.tensor(a + 1e-3 * g.standard_normal(a.shape), dtype=torch.float32) for a in A]
+    Us, lam, fits = pasta.cp_als(X, 3, max_sweeps=80, tol=0.0, init=init)
+    assert fits[-1] > 1.0 - 1e-5, fits[-5:]
+    model = np.einsum("ir,jr,kr,r->ijk", *[u.cpu().double().numpy() for u in Us], lam.cpu().numpy())
+    assert G.rel_err(model, Xd) < 1e-4
+    X.close()
+
+
+def test_singular_normal_equations_are_reported():
+    """A factor column that no stored entry reaches becomes zero; the next
+    mode's V is then singular (the oracle's solve raises on the same input)."""
+    idx = [torch.tensor([0, 1], dtype=torch.int32, device=G.DEV)] * 3
+    val = torch.tensor([1.0, 2.0], device=G.DEV)
+    X = pasta.CooTensor((3, 3, 3), idx, val)
+    col = torch.tensor([[1.0, 0.0], [0.0, 0.0], [0.0, 1.0]])
+    Us = [torch.eye(3)[:, :2].contiguous(), col.clone(), col.clone()]
+    with pytest.raises(np.linalg.LinAlgError):
+        oracle.cp_als_sweep((3, 3, 3), [i.cpu().numpy() for i in idx], val.cpu().double().numpy(),
+                            [u.double().numpy() for u in Us])
+    with pytest.raises(pasta.PastaError) as e:
+        pasta.cp_als_sweep(X, [u.to(G.DEV) for u in Us])
+    assert e.value.name == "PASTA_ERR_SINGULAR"
+    X.close()
+
+
+def test_abi_rejects_bad_arguments():
+    wl, X, idx, val, Ud, Uh = _setup("uniform3d_200", 5_000, (50, 40, 30), 16)
+    L = _lib.lib()
+    lam = torch.empty(200, dtype=torch.float64, device=G.DEV)
+    ptrs = _lib.ptr_array([u.data_ptr() for u in Ud])
+    s = torch.cuda.current_stream().cuda_stream
+    # no sorted copies yet
+    assert L.pasta_cp_als_sweep(X.handle, ptrs, 16, lam.data_ptr(), None, s) == 5
+    X.sort_all()
+    assert L.pasta_cp_als_sweep(X.handle, ptrs, 129, lam.data_ptr(), None, s) in (1, 8)
+    assert L.pasta_cp_als_sweep(X.handle, ptrs, 16, None, None, s) == 1
+    assert L.pasta_cp_als_sweep(X.handle, None, 16, lam.data_ptr(), None, s) == 1
+    assert L.pasta_cp_als_sweep(X.handle, ptrs, 16, lam.data_ptr(), None, s) == 0
+    X.close()
+
+
+def test_driver_stops_on_tolerance():
+    wl, X, idx, val, Ud, Uh = _setup("uniform3d_200", 20_000, (200, 200, 200), 8)
+    Us, lam, fits = pasta.cp_als(X, 8, max_sweeps=200, tol=1e-3, init=[u.cpu() for u in Ud])
+    assert len(fits) < 200 and abs(fits[-1] - fits[-2]) < 1e-3
+    X.close()

@@ -103,3 +103,33 @@ def test_cploss3d_20M_loss_and_grad():
                 assert G.rel_err(got, refg) < G.FP32_TOL, (dtype, bwd_mode, k)
     X.close()
     torch.cuda.empty_cache()
+
+
+def test_zipf3d_100M_als_sweep_normal_equations():
+    """One CP-ALS sweep at full size.  After it, the last mode solves its
+    least-squares problem: (U_2 diag(lam)) V = MTTKRP_2 with V the Hadamard
+    product of the final U_0, U_1 Gram matrices, checked at sampled rows of
+    MTTKRP_2 computed by the oracle from the entries reaching them.  Each
+    column of every factor has unit norm, and since U_2 = 0 is a feasible
+    update, 0 <= fit <= 1."""
+    wl = synth.WORKLOADS["zipf3d"]
+    Xd = synth.generate(wl, device=G.DEV)
+    X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
+    idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
+    val = Xd.val.cpu().numpy().astype(np.float64)
+    del Xd
+    U = [u.to(G.DEV).contiguous() for u in synth.factors_for(wl)]
+    lam, fit = pasta.cp_als_sweep(X, U)
+    Uh = [u.cpu().double().numpy() for u in U]
+    lam = lam.cpu().numpy()
+    n = 2
+    V = (Uh[0].T @ Uh[0]) * (Uh[1].T @ Uh[1])
+    rows = sample_rows(idx[n], wl.dims[n], np.random.default_rng(1))
+    sidx, sval = subset(idx, val, n, rows, wl.dims[n])
+    M = oracle.mttkrp(wl.dims, sidx, sval, Uh, n)[rows]
+    assert G.rel_err((Uh[n][rows] * lam[None, :]) @ V, M) < 1e-4
+    for u in Uh:
+        assert np.allclose(np.linalg.norm(u, axis=0), 1.0, atol=1e-5)
+    assert 0.0 <= float(fit) <= 1.0
+    X.close()
+    torch.cuda.empty_cache()
