@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-loss-compare", action="store_true")
+    ap.add_argument("--no-als", action="store_true")
     ap.add_argument("--nnz", type=float, default=None,
                     help="run the workload's distributions and dims at this many entries "
                          "(small cases for profiling; not a bench line)")
@@ -138,8 +139,8 @@ def measured_peak_gbs():
 
 # Kernel groups of the step and the sources their kernels are built from.
 KERNEL_SOURCES = {
-    "mttkrp": ("stream_kernels.cuh", "stream.cu", "mttkrp.cu"),
-    "loss_fwd_bwd": ("stream_kernels.cuh", "stream.cu", "cp_loss.cu"),
+    "mttkrp": ("stream_kernels.cuh", "stream_launch.cuh", "stream_mttkrp.cu", "mttkrp.cu"),
+    "loss_fwd_bwd": ("stream_kernels.cuh", "stream_launch.cuh", "stream_loss_bwd.cu", "cp_loss.cu"),
 }
 KERNEL_NAMES = {
     "mttkrp": "k_stream<T, N, 0, ...> (MTTKRP)",
@@ -203,10 +204,13 @@ def run_own(args, rank, world, local):
     t_sort = []
     for n in range(N):
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
         X.sort_by_mode(n)
+        e1.record()
         torch.cuda.synchronize()
-        t_sort.append((time.perf_counter() - t0) * 1e3)
+        t_sort.append(e0.elapsed_time(e1))
     X.sort_by_mode(0)
     Ms = [torch.empty((wl.dims[n], wl.R), device=dev) for n in range(N)]
     stream = torch.cuda.current_stream()
@@ -291,13 +295,15 @@ def run_own(args, rank, world, local):
         "rooflines": rooflines,
         "breakdown_ms": {"mttkrp_per_mode": [round(x, 4) for x in per_mode_ms],
                          "loss_fwd_bwd": round(loss_ms, 4)},
-        "preprocess": {"sort_ms_per_mode": [round(x, 2) for x in t_sort]},
+        "preprocess": sort_roofline(t_sort, nnz, N, peak),
         "gpu_launches": args.steps * (N + N + 1),
         "clocks": clk,
     }
     del Xd
     torch.cuda.empty_cache()
 
+    if not args.no_als and rank == 0:
+        result["cp_als"] = als_timing(pasta, X, Us, wl, args, sweep_ms)
     if not args.no_loss_compare and rank == 0:
         result["cp_loss"] = loss_compare(pasta, synth, dev, args)
     if not args.no_e2e:
@@ -310,6 +316,45 @@ def run_own(args, rank, world, local):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def sort_roofline(t_sort, nnz, N, peak):
+    """Mode sorts (preprocessing, timed once per mode with CUDA events; the
+    first includes growing the scratch pool).  Compulsory bytes per mode: read
+    the creation-order copy (N indices + value) and write the sorted copy
+    (N indices + value + the 32-bit permutation)."""
+    alg = nnz * (8 * N + 12)
+    ms = sum(t_sort) / len(t_sort)
+    achieved = alg / (ms * 1e-3) / 1e9
+    return {"sort_ms_per_mode": [round(x, 2) for x in t_sort], "alg_bytes_per_mode": alg,
+            "achieved_gbs": round(achieved, 1), "frac": round(achieved / peak, 4),
+            "note": "8-bit LSD radix passes over (key, perm) pairs; each pass moves 32 bytes per entry"}
+
+
+def als_timing(pasta, X, Us, wl, args, mttkrp_ms):
+    """CP-ALS sweeps (pasta_cp_als_sweep) on the benchmark tensor from the
+    benchmark's factors: one warm-up sweep, then K timed with CUDA events
+    (each sweep ends with one stream synchronisation for its status)."""
+    import torch
+    U = [u.clone() for u in Us]
+    pasta.cp_als_sweep(X, U)
+    K = max(3, args.steps // 2)
+    fits = []
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        _, fit = pasta.cp_als_sweep(X, U)
+        fits.append(fit)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / K
+    return {"workload": f"{wl.name}, R={wl.R} FP32, factors from the benchmark start",
+            "sweeps_timed": K, "ms_per_sweep": round(ms, 4),
+            "mttkrp_ms_per_sweep": round(mttkrp_ms, 4),
+            "other_ms_per_sweep": round(ms - mttkrp_ms, 4),
+            "fit_after_each": [round(float(f), 6) for f in fits]}
 
 
 def loss_compare(pasta, synth, dev, args):
