@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-loss-compare", action="store_true")
     ap.add_argument("--no-als", action="store_true")
+    ap.add_argument("--factor-dtype", default="f32", choices=["f32", "bf16", "f16"],
+                    help="factor storage type of the timed step (FP32 accumulation either way)")
     ap.add_argument("--nnz", type=float, default=None,
                     help="run the workload's distributions and dims at this many entries "
                          "(small cases for profiling; not a bench line)")
@@ -197,7 +199,8 @@ def run_own(args, rank, world, local):
     N = wl.order
     # ---- inputs, resident in HBM
     Xd = synth.generate(wl, device=dev)
-    Us = synth.factors_for(wl, device=dev)
+    fdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[args.factor_dtype]
+    Us = [u.to(fdt).contiguous() for u in synth.factors_for(wl, device=dev)]
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     # rows of each factor touched (algorithmic bytes), counted before timing
     touched = [int(torch.unique(ix).numel()) for ix in Xd.idx]
@@ -259,10 +262,10 @@ def run_own(args, rank, world, local):
 
     nnz = wl.nnz
     value = world * N * nnz / (sweep_ms * 1e-3)
-    # Algorithmic (compulsory) bytes, FP32 factors (s = 4): each pass over the
+    # Algorithmic (compulsory) bytes, factor element size s: each pass over the
     # COO stream reads N 32-bit indices and one FP32 value per entry; every
     # factor row the pass needs is read once; each output row written once.
-    es = 4
+    es = Us[0].element_size()
     coo = nnz * (4 * N + 4)
     rows = [touched[k] * wl.R * es for k in range(N)]
     out = [wl.dims[n] * wl.R * 4 for n in range(N)]
@@ -276,7 +279,8 @@ def run_own(args, rank, world, local):
         achieved = sum(bytes_per_launch) / (ms * 1e-3) / 1e9
         rooflines[kname] = {
             "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": profiled_traffic(kname, args.workload),
+            "frac": round(achieved / peak, 4),
+            "traffic": profiled_traffic(kname, args.workload) if args.factor_dtype == "f32" else None,
             "kernel": KERNEL_NAMES[kname], "group": kname, "launches_per_step": launches,
             "ms_per_step": round(ms, 4),
             "alg_bytes_per_launch": bytes_per_launch,
@@ -287,7 +291,7 @@ def run_own(args, rank, world, local):
     result = {
         "metric": METRIC, "value": value, "unit": "nnz/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": args.factor_dtype, "data": "synthetic",
         "config": {"workload": workload_desc(wl), "step": "MTTKRP every mode + CP loss and all gradients (one pass per mode over its sorted copy, the first also summing the loss)",
                    "l2": "no flush: inputs larger than L2 (COO stream 1.6 GB)",
                    "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
@@ -302,7 +306,7 @@ def run_own(args, rank, world, local):
     del Xd
     torch.cuda.empty_cache()
 
-    if not args.no_als and rank == 0:
+    if not args.no_als and rank == 0 and args.factor_dtype == "f32":
         result["cp_als"] = als_timing(pasta, X, Us, wl, args, sweep_ms)
     if not args.no_loss_compare and rank == 0:
         result["cp_loss"] = loss_compare(pasta, synth, dev, args)

@@ -126,9 +126,11 @@ pasta_status pasta_coo_info(pasta_coo X, int *order, uint64_t *dims, uint64_t *n
  * is stable, so entries with equal keys keep creation order.  The copy holds
  * sorted indices, values and the permutation perm (sorted position p holds
  * creation-order entry perm[p]).  A second call for the same mode is a no-op.
- * Temporary device memory (about 21 bytes per entry) comes from a
- * library-owned stream-ordered pool that keeps it for the next sort;
- * pasta_coo_destroy returns the pool's unused memory.
+ * Temporary device memory (about 21 bytes per entry) is the handle's scratch
+ * buffer: allocated on first use (cudaMalloc, which waits for the device),
+ * reused by later sorts and CP-ALS sweeps on the handle, grown when a call
+ * needs more, freed by pasta_coo_destroy.  Calls on one handle that use it
+ * must be ordered (one stream, or synchronised between streams).
  */
 pasta_status pasta_coo_sort_by_mode(pasta_coo X, int mode, void *stream);
 
@@ -305,7 +307,8 @@ pasta_status pasta_convert_scaled(const void *d_src, pasta_dtype src_dtype, void
  *   d_lambda  device output, R doubles: lam of the last mode
  *   d_fit     device output (one double) or NULL
  * Every mode-sorted copy must exist (PASTA_ERR_NOT_SORTED).  Scratch
- * (dims_max x R floats plus small R x R buffers) comes from the library pool.
+ * (dims_max x R floats plus small R x R buffers) is the handle's scratch
+ * buffer (see pasta_coo_sort_by_mode).
  * The call synchronises `stream` once, at its end, to read the solve status:
  * PASTA_ERR_SINGULAR when some V has a non-positive pivot (for example a
  * factor column that became zero); the factors then hold unspecified values.

@@ -6,7 +6,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <mutex>
 #include <new>
 
 #include "pasta_internal.cuh"
@@ -30,46 +29,28 @@ pasta_status cuda_fail(cudaError_t e, const char *where) {
     return e == cudaErrorMemoryAllocation ? PASTA_ERR_NOMEM : PASTA_ERR_CUDA;
 }
 
-// Scratch memory (the sort's keys and histograms) comes from one
-// library-owned stream-ordered pool per device whose release threshold is
-// unbounded, so consecutive sorts reuse the mapped memory instead of mapping
-// it anew after every synchronisation.  pasta_coo_destroy trims the pools.
-namespace {
-constexpr int kMaxDevices = 64;
-std::mutex g_pool_mu;
-cudaMemPool_t g_pools[kMaxDevices] = {};
-}  // namespace
-
-cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= kMaxDevices) return cudaMallocAsync(p, bytes, s);
-    cudaMemPool_t pool;
-    {
-        std::lock_guard<std::mutex> lock(g_pool_mu);
-        if (!g_pools[dev]) {
-            cudaMemPoolProps props{};
-            props.allocType = cudaMemAllocationTypePinned;
-            props.location.type = cudaMemLocationTypeDevice;
-            props.location.id = dev;
-            e = cudaMemPoolCreate(&g_pools[dev], &props);
-            if (e != cudaSuccess) {
-                g_pools[dev] = nullptr;
-                return e;
-            }
-            uint64_t keep = UINT64_MAX;
-            cudaMemPoolSetAttribute(g_pools[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+// Scratch of one handle (sort keys and histograms, CP-ALS buffers): one
+// plain device allocation that only grows, kept until pasta_coo_destroy, so
+// successive sorts and sweeps on a handle reuse it.  Growing it waits for the
+// device, as cudaFree does.  Calls on one handle are stream-ordered, so its
+// users never overlap.
+pasta_status handle_scratch(pasta_coo_s *X, size_t bytes, void **out) {
+    if (bytes > X->scratch_bytes) {
+        if (X->scratch) cudaFree(X->scratch);
+        X->scratch = nullptr;
+        X->scratch_bytes = 0;
+        const size_t grow = (bytes + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
+        cudaError_t e = cudaMalloc(&X->scratch, grow);
+        if (e != cudaSuccess) {
+            X->scratch = nullptr;
+            cudaGetLastError();
+            set_error("cudaMalloc of %zu bytes of scratch failed", grow);
+            return PASTA_ERR_NOMEM;
         }
-        pool = g_pools[dev];
+        X->scratch_bytes = grow;
     }
-    return cudaMallocFromPoolAsync(p, bytes, pool, s);
-}
-
-void scratch_trim() {
-    std::lock_guard<std::mutex> lock(g_pool_mu);
-    for (int d = 0; d < kMaxDevices; ++d)
-        if (g_pools[d]) cudaMemPoolTrimTo(g_pools[d], 0);
+    *out = X->scratch;
+    return PASTA_OK;
 }
 
 size_t dtype_size(pasta_dtype t) {
@@ -303,8 +284,8 @@ pasta_status pasta_coo_destroy(pasta_coo X) {
     for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(X->sorted[k]);
     if (X->partials) cudaFree(X->partials);
     if (X->als_normsq) cudaFree(X->als_normsq);
+    if (X->scratch) cudaFree(X->scratch);
     delete X;
-    scratch_trim();
     return PASTA_OK;
 }
 

@@ -462,7 +462,7 @@ pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *la
     for (int k = 0; k < N; ++k) imax = std::max(imax, X->dims[k]);
     const int nblk = 2 * X->num_sms;  // k_gram grid cap
 
-    // one scratch allocation, 256-byte aligned pieces
+    // the handle's scratch, cut into 256-byte aligned pieces
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -479,7 +479,12 @@ pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *la
                               sizeof(double));
     const size_t oStatus = take(sizeof(int));
     char *base = nullptr;
-    PASTA_CUDA(scratch_alloc((void **)&base, off, s));
+    {
+        void *p = nullptr;
+        const pasta_status hs = handle_scratch(X, off, &p);
+        if (hs != PASTA_OK) return hs;
+        base = static_cast<char *>(p);
+    }
     float *M = reinterpret_cast<float *>(base + oM);
     double *G = reinterpret_cast<double *>(base + oG);
     float *W = reinterpret_cast<float *>(base + oW);
@@ -489,10 +494,7 @@ pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *la
     double *part = reinterpret_cast<double *>(base + oPart);
     int *status = reinterpret_cast<int *>(base + oStatus);
 
-    auto fail = [&](pasta_status e) {
-        cudaFreeAsync(base, s);
-        return e;
-    };
+    auto fail = [&](pasta_status e) { return e; };
     cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
     if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(status)"));
 
@@ -531,7 +533,6 @@ pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *la
 
     int h_status = 0;
     e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
-    cudaFreeAsync(base, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "CP-ALS status read");
     if (h_status != 0) {

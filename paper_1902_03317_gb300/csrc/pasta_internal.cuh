@@ -21,10 +21,6 @@ constexpr uint64_t kPadEntries = 1024;    // stored arrays are padded to this mu
 
 void set_error(const char *fmt, ...);
 pasta_status cuda_fail(cudaError_t e, const char *where);
-// Stream-ordered scratch from the library's per-device pool (release with
-// cudaFreeAsync); scratch_trim returns the pools' unused memory.
-cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
-void scratch_trim();
 
 #define PASTA_CUDA(call)                                         \
     do {                                                         \
@@ -58,7 +54,14 @@ struct pasta_coo_s {
     double *partials = nullptr;  // per-block FP64 partial sums of the loss
     int partials_cap = 0;
     double *als_normsq = nullptr;  // CP-ALS: sum of squared values (device), computed once
+    void *scratch = nullptr;       // grow-only scratch (handle_scratch)
+    size_t scratch_bytes = 0;
 };
+
+namespace pasta {
+// At least `bytes` of the handle's scratch (see api.cu); PASTA_ERR_NOMEM on failure.
+pasta_status handle_scratch(pasta_coo_s *X, size_t bytes, void **out);
+}  // namespace pasta
 
 namespace pasta {
 

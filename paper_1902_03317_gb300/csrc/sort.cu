@@ -350,19 +350,16 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
     const int passes = (used + 7) / 8;
 
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
-    uint64_t *keys = nullptr;
-    uint32_t *tmpv = nullptr, *hist = nullptr;
+    // scratch: two key buffers, the spare permutation buffer, the histograms
     const size_t hist_n = (size_t)256 * ntiles + 256;
-    PASTA_CUDA(scratch_alloc((void **)&keys, 2 * n * sizeof(uint64_t), s));
-    cudaError_t e1 = scratch_alloc((void **)&tmpv, n * sizeof(uint32_t), s);
-    cudaError_t e2 = scratch_alloc((void **)&hist, hist_n * sizeof(uint32_t), s);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) {
-        cudaFreeAsync(keys, s);
-        if (tmpv) cudaFreeAsync(tmpv, s);
-        if (hist) cudaFreeAsync(hist, s);
-        set_error("allocation of sort scratch failed");
-        return PASTA_ERR_NOMEM;
-    }
+    const size_t keys_b = (2 * n * sizeof(uint64_t) + 255) & ~(size_t)255;
+    const size_t tmpv_b = (n * sizeof(uint32_t) + 255) & ~(size_t)255;
+    void *base = nullptr;
+    pasta_status sst = handle_scratch(X, keys_b + tmpv_b + hist_n * sizeof(uint32_t), &base);
+    if (sst != PASTA_OK) return sst;
+    uint64_t *keys = reinterpret_cast<uint64_t *>(base);
+    uint32_t *tmpv = reinterpret_cast<uint32_t *>(static_cast<char *>(base) + keys_b);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(static_cast<char *>(base) + keys_b + tmpv_b);
     uint64_t *kb[2] = {keys, keys + n};
     uint32_t *vb[2];
     vb[passes % 2] = dst.perm;  // the last pass writes into the copy's perm
@@ -402,9 +399,6 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
     k_gather<<<gblocks, 256, 0, s>>>(src, dst.perm, kb[passes % 2], gd);
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) st = cuda_fail(le, "sort kernels");
-    cudaFreeAsync(keys, s);
-    cudaFreeAsync(tmpv, s);
-    cudaFreeAsync(hist, s);
     return st;
 }
 
