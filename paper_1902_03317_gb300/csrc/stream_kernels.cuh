@@ -37,6 +37,14 @@ __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x
 
 enum Kind : int { kMttkrp = 0, kLossFwd = 1, kLossBwd = 2 };
 
+// Entries per lane-group tile (at least one chunk of 4L).  A block tile is
+// kWarps * G group tiles; blocks synchronise once per block tile.
+#ifndef PASTA_STREAM_GROUP_TILE
+#define PASTA_STREAM_GROUP_TILE 512
+#endif
+constexpr int kGroupTile = PASTA_STREAM_GROUP_TILE;
+__host__ __device__ constexpr int group_tile(int L) { return 4 * L > kGroupTile ? 4 * L : kGroupTile; }
+
 template <typename T, int N>
 struct Args {
     const uint32_t *idx[N];  // position p holds mode (rot + p) % N; position 0 is the sorted mode
@@ -259,7 +267,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
     const int lig = lane & (L - 1);
     const int grp = lane >> lshift;
     const int G = 32 >> lshift;
-    const int tile = LC ? (4 * LC > 512 ? 4 * LC : 512) : a.tile;  // as make_geometry
+    const int tile = LC ? group_tile(LC) : a.tile;
     const int chunk = 4 * L;
     const int GS = 4 * L + 4;  // padded words per group chunk (bank spread)
     const int AS = G * GS;     // words per array per stage

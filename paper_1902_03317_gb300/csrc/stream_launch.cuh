@@ -50,14 +50,14 @@ pasta_status run(const StreamLaunch &l, cudaStream_t s) {
     if (LC != 0 && g.L != LC) return PASTA_ERR_UNSUPPORTED;  // by_lanes picks LC = L
     a.L = g.L;
     a.lshift = g.lshift;
-    a.tile = g.tile;
+    a.tile = stream::group_tile(g.L);
     const size_t smem = stream::smem_bytes(N, kStages, g.L, l.R);
     auto kern = k_stream<T, N, KIND, kStages, MINB, LC>;
     PASTA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PASTA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     per_sm = std::max(per_sm, 1);
-    const uint64_t span = (uint64_t)g.tile * (uint64_t)(32 >> g.lshift) * kWarps;
+    const uint64_t span = (uint64_t)a.tile * (uint64_t)(32 >> g.lshift) * kWarps;
     const uint64_t nbt = std::max<uint64_t>(1, (l.nnz + span - 1) / span);
     uint64_t blocks = std::min<uint64_t>(nbt, (uint64_t)l.num_sms * (uint64_t)per_sm);
     if (l.max_blocks > 0) blocks = std::min<uint64_t>(blocks, (uint64_t)l.max_blocks);
