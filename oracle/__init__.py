@@ -223,3 +223,95 @@ def cp_fit(val, U, lam, M_last) -> float:
     inner = float(np.sum(lam * np.sum(np.asarray(M_last) * U[-1], axis=0)))
     res2 = max(normx2 + norm_model2 - 2.0 * inner, 0.0)
     return 1.0 - np.sqrt(res2) / np.sqrt(normx2) if normx2 > 0 else 0.0
+
+
+# ------------------------------------------------------------ TEW-eq, TS ---
+#
+# Element-wise operations between two tensors with the same coordinates
+# (TEW-eq, Sec. 3.1 and Algorithm 1) and between a tensor and a scalar (TS,
+# Sec. 3.2 and Algorithm 3).  The coordinates pass through unchanged; only the
+# values are combined.  FP64 arithmetic on the (FP32) stored values; the GPU
+# computes in FP32, so parity is stated in FP32 units in the last place.
+
+OPS = ("add", "sub", "mul", "div")
+
+
+def _apply(op: str, a, b):
+    if op == "add":
+        return a + b
+    if op == "sub":
+        return a - b
+    if op == "mul":
+        return a * b
+    if op == "div":
+        with np.errstate(divide="ignore", invalid="ignore"):
+            return a / b
+    raise ValueError(f"unknown op {op!r}")
+
+
+def tew_eq(idx_x, val_x, idx_y, val_y, op: str):
+    """Z = X op Y for tensors with identical coordinate lists (Algorithm 1).
+    Returns (idx_z, val_z) in FP64; raises if the coordinates differ."""
+    for a, b in zip(idx_x, idx_y):
+        if not np.array_equal(np.asarray(a), np.asarray(b)):
+            raise ValueError("TEW-eq needs the same coordinates in the same order")
+    vx = np.asarray(val_x, dtype=np.float64)
+    vy = np.asarray(val_y, dtype=np.float64)
+    return [np.asarray(a).copy() for a in idx_x], _apply(op, vx, vy)
+
+
+def ts(idx_x, val_x, op: str, s: float):
+    """Y = X op s for every stored entry (Algorithm 3 for multiplication;
+    the other operators alike).  Returns (idx_y, val_y) in FP64."""
+    vx = np.asarray(val_x, dtype=np.float64)
+    return [np.asarray(a).copy() for a in idx_x], _apply(op, vx, np.float64(s))
+
+
+# -------------------------------------------------------------- TTV, TTM ---
+#
+# Mode-n products (Sec. 3.3 and 3.4, Algorithms 4 and 5).  The result keeps
+# one entry per mode-n fiber of X (the stored entries sharing every index but
+# i_n), Y(f, r) = sum over the fiber's entries of x * U(i_n, r) (TTV: R = 1,
+# U = v).  Fibers are listed in lexicographic order of their coordinates in
+# the cyclic mode order n+1, ..., N-1, 0, ..., n-1 (numpy.lexsort as a library
+# step), the order in which the mode-(n+1) sorted copy holds them.
+
+def fiber_modes(order: int, mode: int) -> list[int]:
+    """The modes of a mode-n fiber's coordinates, in cyclic order from n+1."""
+    return [(mode + j) % order for j in range(1, order)]
+
+
+def ttm(dims, idx, val, U, mode: int):
+    """Y = X x_n U with U of shape dims[mode] x R (the paper's transposed
+    convention).  Returns (fiber_coords: list of N-1 uint32 arrays, in the
+    modes of fiber_modes(), Y: nfibs x R FP64)."""
+    N = len(dims)
+    U = np.asarray(U, dtype=np.float64)
+    if U.ndim == 1:
+        U = U[:, None]
+    modes = fiber_modes(N, mode)
+    idx = [np.asarray(ix).astype(np.int64) for ix in idx]
+    val = np.asarray(val, dtype=np.float64)
+    acc: dict[tuple, np.ndarray] = {}
+    for m in range(val.shape[0]):
+        key = tuple(int(idx[k][m]) for k in modes)
+        row = acc.get(key)
+        if row is None:
+            row = np.zeros(U.shape[1])
+            acc[key] = row
+        row += val[m] * U[int(idx[mode][m])]
+    keys = list(acc.keys())
+    if not keys:
+        return [np.zeros(0, dtype=np.uint32) for _ in modes], np.zeros((0, U.shape[1]))
+    K = np.array(keys, dtype=np.int64)
+    order = np.lexsort(K.T[::-1])
+    coords = [K[order, j].astype(np.uint32) for j in range(len(modes))]
+    Y = np.stack([acc[keys[i]] for i in order])
+    return coords, Y
+
+
+def ttv(dims, idx, val, v, mode: int):
+    """Y = X x_n v (Algorithm 4): TTM with a single column.  Returns
+    (fiber_coords, y with one value per fiber)."""
+    coords, Y = ttm(dims, idx, val, np.asarray(v, dtype=np.float64)[:, None], mode)
+    return coords, Y[:, 0]
