@@ -48,6 +48,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-loss-compare", action="store_true")
     ap.add_argument("--no-als", action="store_true")
+    ap.add_argument("--no-tew", action="store_true")
     ap.add_argument("--factor-dtype", default="f32", choices=["f32", "bf16", "f16"],
                     help="factor storage type of the timed step (FP32 accumulation either way)")
     ap.add_argument("--nnz", type=float, default=None,
@@ -316,6 +317,8 @@ def run_own(args, rank, world, local):
     del Xd
     torch.cuda.empty_cache()
 
+    if not args.no_tew and rank == 0:
+        result["tew_ts"] = tew_ts_timing(pasta, X, N, nnz, peak, args)
     if not args.no_als and rank == 0 and args.factor_dtype == "f32":
         result["cp_als"] = als_timing(pasta, X, Us, wl, args, sweep_ms)
     if not args.no_loss_compare and rank == 0:
@@ -369,6 +372,37 @@ def als_timing(pasta, X, Us, wl, args, mttkrp_ms):
             "mttkrp_ms_per_sweep": round(mttkrp_ms, 4),
             "other_ms_per_sweep": round(ms - mttkrp_ms, 4),
             "fit_after_each": [round(float(f), 6) for f in fits]}
+
+
+def tew_ts_timing(pasta, X, N, nnz, peak, args):
+    """TS (Z = X * s) and TEW-eq (Z = X + Y) on the benchmark tensor into a
+    reused output handle, K calls each timed with CUDA events.  Compulsory
+    bytes per entry: TS reads X's N indices and value and writes Z's (8N + 8);
+    TEW-eq also reads Y's value and, to check the shared coordinates, Y's N
+    indices (12N + 12).  TEW-eq synchronises once per call (the check)."""
+    import torch
+    Y = pasta.ts(X, "mul", 0.5)
+    Z = pasta.ts(X, "add", 1.0)
+    out = {}
+    K = max(3, args.steps // 3)
+    for name, call, per_entry in (("ts_mul", lambda: pasta.ts(X, "mul", 1.5, out=Z), 8 * N + 8),
+                                  ("tew_eq_add", lambda: pasta.tew_eq(X, Y, "add", out=Z), 12 * N + 12)):
+        call()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(K):
+            call()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / K
+        gbs = per_entry * nnz / (ms * 1e-3) / 1e9
+        out[name] = {"ms_per_call": round(ms, 4), "alg_bytes_per_call": per_entry * nnz,
+                     "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4), "calls_timed": K}
+    Y.close()
+    Z.close()
+    return out
 
 
 def loss_compare(pasta, synth, dev, args):

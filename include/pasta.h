@@ -316,6 +316,41 @@ pasta_status pasta_convert_scaled(const void *d_src, pasta_dtype src_dtype, void
 pasta_status pasta_cp_als_sweep(pasta_coo X, float *const *d_U, int R, double *d_lambda,
                                 double *d_fit, void *stream);
 
+/* Element-wise operators of TEW-eq and TS (Sec. 3.1, 3.2). */
+typedef enum {
+    PASTA_OP_ADD = 0,
+    PASTA_OP_SUB = 1,
+    PASTA_OP_MUL = 2,
+    PASTA_OP_DIV = 3
+} pasta_op;
+
+/*
+ * pasta_tew_eq -- Z = X op Y for two tensors with exactly the same stored
+ * coordinates in the same order (TEW-eq, Sec. 3.1 and Algorithm 1): every
+ * stored value z_m = x_m op y_m, computed in FP32 with IEEE rounding (a
+ * division by a stored zero gives Inf or NaN; Z is not validated).
+ *   X, Y   same order, dims and nnz, else PASTA_ERR_INVALID_ARG; the
+ *          creation-order coordinates are compared on the device (one pass,
+ *          then one synchronisation of `stream`) and PASTA_ERR_INVALID_ARG is
+ *          returned if any differs
+ *   op     PASTA_OP_ADD / SUB / MUL / DIV
+ *   Z      in/out: *Z == NULL makes a new handle (caller destroys it);
+ *          otherwise *Z must be a handle of the same order, dims and nnz,
+ *          neither X nor Y, and its creation-order copy is overwritten (its
+ *          sorted copies and fiber tables are dropped)
+ * Z holds only a creation-order copy: X's coordinates and the new values.
+ */
+pasta_status pasta_tew_eq(pasta_coo X, pasta_coo Y, pasta_op op, pasta_coo *Z, void *stream);
+
+/*
+ * pasta_ts -- Z = X op s for every stored value (TS, Sec. 3.2 and
+ * Algorithm 3), in FP32 with s rounded to FP32 once.  Z as for
+ * pasta_tew_eq (new, or a same-shaped handle that is neither X).  The paper
+ * reduces subtraction and division to addition and multiplication by -s and
+ * 1/s; here all four are computed directly (x / s is correctly rounded).
+ */
+pasta_status pasta_ts(pasta_coo X, pasta_op op, double s, pasta_coo *Z, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

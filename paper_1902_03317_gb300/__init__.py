@@ -6,8 +6,8 @@ and a thin torch-facing API.  Nothing here computes on the CPU: if the
 library is missing, calls fail with a RuntimeError.
 """
 from .api import (CooTensor, CPLoss, acc_dtype, convert, cp_als, cp_als_sweep, cp_loss,  # noqa: F401
-                  cp_loss_bwd, cp_loss_fwd, cp_loss_fwd_bwd, mttkrp)
+                  cp_loss_bwd, cp_loss_fwd, cp_loss_fwd_bwd, mttkrp, tew_eq, ts)
 from ._lib import PastaError  # noqa: F401
 
 __all__ = ["CooTensor", "CPLoss", "cp_loss", "cp_loss_fwd", "cp_loss_bwd", "cp_loss_fwd_bwd", "mttkrp",
-           "cp_als_sweep", "cp_als", "convert", "acc_dtype", "PastaError"]
+           "cp_als_sweep", "cp_als", "tew_eq", "ts", "convert", "acc_dtype", "PastaError"]

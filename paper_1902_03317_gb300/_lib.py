@@ -18,6 +18,7 @@ PASTA_CREATE_DEFAULT, PASTA_CREATE_NO_VALIDATE = 0, 1
 MAX_ORDER = 8
 MAX_RANK = 256
 ALS_MAX_RANK = 128
+OPS = {"add": 0, "sub": 1, "mul": 2, "div": 3}  # pasta_op
 
 STATUS = {
     0: "PASTA_OK", 1: "PASTA_ERR_INVALID_ARG", 2: "PASTA_ERR_ALIGNMENT",
@@ -48,6 +49,8 @@ SIGNATURES = {
     "pasta_cp_loss_fwd_bwd": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
     "pasta_cp_loss_fwd_noalloc": (_I, [_I, _P, _U64, _P, _P, _P, _I, _I, _P, _P, _P]),
     "pasta_cp_als_sweep": (_I, [_P, _P, _I, _P, _P, _P]),
+    "pasta_tew_eq": (_I, [_P, _P, _I, _P, _P]),
+    "pasta_ts": (_I, [_P, _I, ctypes.c_double, _P, _P]),
 }
 
 _lock = threading.Lock()

@@ -87,6 +87,15 @@ class CooTensor:
             raise RuntimeError("CooTensor is closed")
         return self._h
 
+    @classmethod
+    def _adopt(cls, handle: ctypes.c_void_p, like: "CooTensor") -> "CooTensor":
+        """Wrap a handle the library created with ``like``'s order, dims and nnz."""
+        t = cls.__new__(cls)
+        t.device, t.dims, t.order, t.nnz = like.device, like.dims, like.order, like.nnz
+        t._h = handle
+        t._sorted = set()
+        return t
+
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:
             _lib.lib().pasta_coo_destroy(self._h)
@@ -124,6 +133,38 @@ class CooTensor:
                 _stream(self.device))
         _lib.check(st, "pasta_coo_copy_out")
         return idx, val, perm
+
+
+def _elementwise_out(X: CooTensor, out: CooTensor | None):
+    if out is None:
+        return ctypes.c_void_p(), None
+    if out is X:
+        raise ValueError("out must differ from the inputs")
+    out._sorted.clear()  # the library drops the output's sorted copies
+    return ctypes.c_void_p(out.handle.value), out
+
+
+def tew_eq(X: CooTensor, Y: CooTensor, op: str, out: CooTensor | None = None) -> CooTensor:
+    """Z = X op Y (``op`` in add/sub/mul/div) for tensors storing the same
+    coordinates in the same order (TEW-eq, Algorithm 1).  Returns a new
+    CooTensor, or writes ``out`` (same shape, neither input) and returns it."""
+    h, o = _elementwise_out(X, out)
+    if o is Y:
+        raise ValueError("out must differ from the inputs")
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_tew_eq(X.handle, Y.handle, _lib.OPS[op], ctypes.byref(h), _stream(X.device))
+    _lib.check(st, "pasta_tew_eq")
+    return o if o is not None else CooTensor._adopt(h, X)
+
+
+def ts(X: CooTensor, op: str, s: float, out: CooTensor | None = None) -> CooTensor:
+    """Z = X op s for every stored value (TS, Algorithm 3), FP32 with s
+    rounded to FP32.  Returns a new CooTensor or writes ``out``."""
+    h, o = _elementwise_out(X, out)
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_ts(X.handle, _lib.OPS[op], float(s), ctypes.byref(h), _stream(X.device))
+    _lib.check(st, "pasta_ts")
+    return o if o is not None else CooTensor._adopt(h, X)
 
 
 def _factor_ptrs(X: CooTensor, Us: Sequence[torch.Tensor | None], skip: int = -1):

@@ -167,35 +167,13 @@ pasta_status validate_coo(const pasta_coo_s *X, void *stream, uint64_t *bad_inde
     return PASTA_OK;
 }
 
-}  // namespace pasta
-
-using namespace pasta;
-
-extern "C" {
-
-const char *pasta_status_str(pasta_status s) {
-    switch (s) {
-        case PASTA_OK: return "PASTA_OK";
-        case PASTA_ERR_INVALID_ARG: return "PASTA_ERR_INVALID_ARG";
-        case PASTA_ERR_ALIGNMENT: return "PASTA_ERR_ALIGNMENT";
-        case PASTA_ERR_INDEX_OOB: return "PASTA_ERR_INDEX_OOB";
-        case PASTA_ERR_NONFINITE: return "PASTA_ERR_NONFINITE";
-        case PASTA_ERR_NOT_SORTED: return "PASTA_ERR_NOT_SORTED";
-        case PASTA_ERR_NOMEM: return "PASTA_ERR_NOMEM";
-        case PASTA_ERR_CUDA: return "PASTA_ERR_CUDA";
-        case PASTA_ERR_UNSUPPORTED: return "PASTA_ERR_UNSUPPORTED";
-        case PASTA_ERR_SINGULAR: return "PASTA_ERR_SINGULAR";
-    }
-    return "PASTA_ERR_UNKNOWN";
-}
-
-const char *pasta_last_error(void) { return g_err; }
-
-int pasta_version(void) { return PASTA_VERSION; }
-
-pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,
-                              const uint32_t *const *d_idx, const float *d_val, unsigned flags,
-                              void *stream) {
+// Handle construction shared by pasta_coo_create and the operations that
+// return a new tensor: copies the caller's (device) coordinates and, when
+// d_val is not NULL, values into a new creation-order copy (zero padding);
+// validates unless PASTA_CREATE_NO_VALIDATE.
+pasta_status make_handle(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,
+                         const uint32_t *const *d_idx, const float *d_val, unsigned flags,
+                         void *stream) {
     if (!out) {
         set_error("out is NULL");
         return PASTA_ERR_INVALID_ARG;
@@ -215,13 +193,9 @@ pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, u
         set_error("nnz must be < 2^32 - 2^16");
         return PASTA_ERR_INVALID_ARG;
     }
-    if (flags & ~PASTA_CREATE_NO_VALIDATE) {
-        set_error("unknown flags 0x%x", flags);
-        return PASTA_ERR_INVALID_ARG;
-    }
     if (nnz > 0) {
-        if (!d_idx || !d_val) {
-            set_error("d_idx/d_val is NULL");
+        if (!d_idx) {
+            set_error("d_idx is NULL");
             return PASTA_ERR_INVALID_ARG;
         }
         for (int k = 0; k < order; ++k)
@@ -253,7 +227,7 @@ pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, u
         e = cudaMemsetAsync(X->orig.block, 0, arr * (size_t)(order + 1), s);
         for (int k = 0; k < order && e == cudaSuccess && nnz > 0; ++k)
             e = cudaMemcpyAsync(X->orig.idx[k], d_idx[k], nnz * 4, cudaMemcpyDeviceToDevice, s);
-        if (e == cudaSuccess && nnz > 0)
+        if (e == cudaSuccess && nnz > 0 && d_val)
             e = cudaMemcpyAsync(X->orig.val, d_val, nnz * 4, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) st = cuda_fail(e, "copy-in");
     }
@@ -275,6 +249,46 @@ pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, u
     }
     *out = X;
     return PASTA_OK;
+}
+
+}  // namespace pasta
+
+using namespace pasta;
+
+extern "C" {
+
+const char *pasta_status_str(pasta_status s) {
+    switch (s) {
+        case PASTA_OK: return "PASTA_OK";
+        case PASTA_ERR_INVALID_ARG: return "PASTA_ERR_INVALID_ARG";
+        case PASTA_ERR_ALIGNMENT: return "PASTA_ERR_ALIGNMENT";
+        case PASTA_ERR_INDEX_OOB: return "PASTA_ERR_INDEX_OOB";
+        case PASTA_ERR_NONFINITE: return "PASTA_ERR_NONFINITE";
+        case PASTA_ERR_NOT_SORTED: return "PASTA_ERR_NOT_SORTED";
+        case PASTA_ERR_NOMEM: return "PASTA_ERR_NOMEM";
+        case PASTA_ERR_CUDA: return "PASTA_ERR_CUDA";
+        case PASTA_ERR_UNSUPPORTED: return "PASTA_ERR_UNSUPPORTED";
+        case PASTA_ERR_SINGULAR: return "PASTA_ERR_SINGULAR";
+    }
+    return "PASTA_ERR_UNKNOWN";
+}
+
+const char *pasta_last_error(void) { return g_err; }
+
+int pasta_version(void) { return PASTA_VERSION; }
+
+pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,
+                              const uint32_t *const *d_idx, const float *d_val, unsigned flags,
+                              void *stream) {
+    if (flags & ~PASTA_CREATE_NO_VALIDATE) {
+        set_error("unknown flags 0x%x", flags);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (nnz > 0 && !d_val) {
+        set_error("d_val is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    return pasta::make_handle(out, order, dims, nnz, d_idx, d_val, flags, stream);
 }
 
 pasta_status pasta_coo_destroy(pasta_coo X) {
@@ -514,6 +528,102 @@ pasta_status pasta_cp_als_sweep(pasta_coo X, float *const *d_U, int R, double *d
         return PASTA_ERR_INVALID_ARG;
     }
     return run_cp_als_sweep(X, d_U, R, d_lambda, d_fit, static_cast<cudaStream_t>(stream));
+}
+
+// Output handle of TEW-eq / TS: a new handle with X's coordinates, or the
+// caller's same-shaped handle with X's coordinates copied over its
+// creation-order copy and its derived data (sorted copies, cached norm)
+// dropped.  *created tells the caller whether to destroy it on failure.
+static pasta_status elementwise_output(pasta_coo X, pasta_coo Y, pasta_coo *Z, cudaStream_t s,
+                                       bool *created) {
+    *created = false;
+    if (!*Z) {
+        pasta_status st = pasta::make_handle(Z, X->order, X->dims, X->nnz,
+                                             const_cast<const uint32_t *const *>(X->orig.idx), nullptr,
+                                             PASTA_CREATE_NO_VALIDATE, s);
+        *created = (st == PASTA_OK);
+        return st;
+    }
+    pasta_coo O = *Z;
+    if (O == X || O == Y) {
+        set_error("the output handle must differ from the inputs");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (O->order != X->order || O->nnz != X->nnz) {
+        set_error("the output handle's order/nnz differ from the input's");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < X->order; ++k)
+        if (O->dims[k] != X->dims[k]) {
+            set_error("the output handle's dims differ from the input's");
+            return PASTA_ERR_INVALID_ARG;
+        }
+    bool derived = O->als_normsq != nullptr;
+    for (int k = 0; k < PASTA_MAX_ORDER; ++k) derived = derived || O->sorted[k].block != nullptr;
+    if (derived) {
+        cudaStreamSynchronize(s);  // earlier work on O may still read what is freed here
+        for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(O->sorted[k]);
+        if (O->als_normsq) {
+            cudaFree(O->als_normsq);
+            O->als_normsq = nullptr;
+        }
+    }
+    for (int k = 0; k < X->order; ++k)
+        PASTA_CUDA(cudaMemcpyAsync(O->orig.idx[k], X->orig.idx[k], (size_t)X->nnz_pad * 4,
+                                   cudaMemcpyDeviceToDevice, s));
+    return PASTA_OK;
+}
+
+static bool ok_op(int op) { return op >= PASTA_OP_ADD && op <= PASTA_OP_DIV; }
+
+pasta_status pasta_tew_eq(pasta_coo X, pasta_coo Y, pasta_op op, pasta_coo *Z, void *stream) {
+    if (!X || !Y || !Z || !ok_op(op)) {
+        set_error("NULL handle/output or unknown op");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (X->order != Y->order || X->nnz != Y->nnz) {
+        set_error("X and Y differ in order or nnz");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < X->order; ++k)
+        if (X->dims[k] != Y->dims[k]) {
+            set_error("X and Y differ in dims[%d]", k);
+            return PASTA_ERR_INVALID_ARG;
+        }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool same = false;
+    pasta_status st = same_coordinates(X, Y, s, &same);
+    if (st != PASTA_OK) return st;
+    if (!same) {
+        set_error("X and Y do not store the same coordinates in the same order");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    bool created = false;
+    st = elementwise_output(X, Y, Z, s, &created);
+    if (st == PASTA_OK)
+        st = launch_elementwise(X->orig.val, Y->orig.val, 0.0, (*Z)->orig.val, X->nnz_pad, op, X->num_sms, s);
+    if (st != PASTA_OK && created) {
+        pasta_coo_destroy(*Z);
+        *Z = nullptr;
+    }
+    return st;
+}
+
+pasta_status pasta_ts(pasta_coo X, pasta_op op, double sc, pasta_coo *Z, void *stream) {
+    if (!X || !Z || !ok_op(op)) {
+        set_error("NULL handle/output or unknown op");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    bool created = false;
+    pasta_status st = elementwise_output(X, nullptr, Z, s, &created);
+    if (st == PASTA_OK)
+        st = launch_elementwise(X->orig.val, nullptr, sc, (*Z)->orig.val, X->nnz_pad, op, X->num_sms, s);
+    if (st != PASTA_OK && created) {
+        pasta_coo_destroy(*Z);
+        *Z = nullptr;
+    }
+    return st;
 }
 
 }  // extern "C"

@@ -61,6 +61,10 @@ struct pasta_coo_s {
 namespace pasta {
 // At least `bytes` of the handle's scratch (see api.cu); PASTA_ERR_NOMEM on failure.
 pasta_status handle_scratch(pasta_coo_s *X, size_t bytes, void **out);
+// New handle from device coordinates (and values unless d_val is NULL); see api.cu.
+pasta_status make_handle(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,
+                         const uint32_t *const *d_idx, const float *d_val, unsigned flags,
+                         void *stream);
 }  // namespace pasta
 
 namespace pasta {
@@ -150,6 +154,14 @@ pasta_status launch_cp_loss_fwd_bwd(const pasta_coo_s *X, const void *const *U, 
 // One CP-ALS sweep (cp_als.cu); arguments checked by the caller.
 pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *lambda, double *fit,
                               cudaStream_t stream);
+
+// TEW-eq / TS (tew.cu): coordinate equality of two creation-order copies
+// (synchronises `stream`), and z = x op y (y == NULL: z = x op s) over n_pad
+// padded values.
+pasta_status same_coordinates(const pasta_coo_s *X, const pasta_coo_s *Y, cudaStream_t stream,
+                              bool *same);
+pasta_status launch_elementwise(const float *x, const float *y, double s, float *z, uint64_t n_pad,
+                                int op, int num_sms, cudaStream_t stream);
 
 pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,
                             uint64_t n, const double *scale, cudaStream_t stream);

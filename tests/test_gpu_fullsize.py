@@ -133,3 +133,32 @@ def test_zipf3d_100M_als_sweep_normal_equations():
     assert 0.0 <= float(fit) <= 1.0
     X.close()
     torch.cuda.empty_cache()
+
+
+def test_zipf3d_100M_tew_eq_and_ts_sampled():
+    """TS and TEW-eq over the full 100M-entry tensor, checked at 1M sampled
+    stored positions against the oracle (coordinates bit-exact, values within
+    1 FP32 ulp; the multiplications exact)."""
+    wl = synth.WORKLOADS["zipf3d"]
+    Xd = synth.generate(wl, device=G.DEV)
+    X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
+    del Xd
+    Y = pasta.ts(X, "mul", -0.37)
+    Z = pasta.tew_eq(X, Y, "div")
+    rng = np.random.default_rng(3)
+    pos = torch.tensor(np.sort(rng.choice(wl.nnz, size=1_000_000, replace=False)), device=G.DEV)
+    xi, xv, _ = X.copy_out()
+    _, yv, _ = Y.copy_out()
+    zi, zv, _ = Z.copy_out()
+    for k in range(3):
+        assert torch.equal(zi[k], xi[k])
+    idx_s = [xi[k][pos].cpu().numpy().astype(np.uint32) for k in range(3)]
+    xs = xv[pos].cpu().double().numpy()
+    _, ys = oracle.ts(idx_s, xs, "mul", float(np.float32(-0.37)))
+    assert np.array_equal(yv[pos].cpu().numpy(), ys.astype(np.float32))
+    _, zs = oracle.tew_eq(idx_s, xs, idx_s, yv[pos].cpu().double().numpy(), "div")
+    from tests.test_gpu_tew import ulp_distance
+    assert ulp_distance(zv[pos].cpu().numpy(), zs).max() <= 1
+    for t in (X, Y, Z):
+        t.close()
+    torch.cuda.empty_cache()
