@@ -351,6 +351,44 @@ pasta_status pasta_tew_eq(pasta_coo X, pasta_coo Y, pasta_op op, pasta_coo *Z, v
  */
 pasta_status pasta_ts(pasta_coo X, pasta_op op, double s, pasta_coo *Z, void *stream);
 
+/*
+ * pasta_coo_fibers -- build (once) the mode-n fiber table, the preprocessing
+ * of Algorithms 4 and 5 (Sec. 5.2: the number of mode-n fibers and where
+ * each begins).  A mode-n fiber is the set of stored entries sharing every
+ * index but i_n; each is a contiguous run of the mode-(n+1 mod N) sorted
+ * copy, which must exist (else PASTA_ERR_NOT_SORTED), and the other modes'
+ * index bits must fit its 64-bit key (else PASTA_ERR_UNSUPPORTED).  Fibers
+ * are numbered in that copy's order: lexicographic in the modes n+1, ...,
+ * N-1, 0, ..., n-1.  *nfibs (host, may be NULL) receives their number.
+ * Synchronises `stream` once (to size the table).  Device memory: 4 bytes
+ * per stored entry plus 4 (N-1) per fiber, freed by pasta_coo_destroy.
+ */
+pasta_status pasta_coo_fibers(pasta_coo X, int mode, uint64_t *nfibs, void *stream);
+
+/* The fibers' coordinates: d_coords is a host array of N-1 device pointers
+ * (nfibs uint32 each; NULL entries are skipped) for modes n+1, ..., n-1
+ * (cyclic).  PASTA_ERR_NOT_SORTED without the fiber table.  Asynchronous. */
+pasta_status pasta_coo_fiber_coords(pasta_coo X, int mode, uint32_t *const *d_coords, void *stream);
+
+/*
+ * pasta_ttm -- mode-n Tensor-Times-Matrix, Eq. (ttm) / Algorithm 5 with the
+ * paper's transposed convention (U is dims[mode] x R, row-major):
+ *     Y(f, r) = sum over the entries m of fiber f of val(m) * U(i_n(m), r).
+ * d_Y: device, nfibs x R row-major, FP32 (FP64 when u_dtype is PASTA_F64),
+ * overwritten (may be NULL when there are no fibers); row f is fiber f of
+ * pasta_coo_fibers.  The fiber table must
+ * exist (PASTA_ERR_NOT_SORTED).  Runs as an MTTKRP of the order-2 tensor
+ * (fiber, i_n), so its accuracy and speed follow pasta_mttkrp's.
+ */
+pasta_status pasta_ttm(pasta_coo X, int mode, const void *d_U, pasta_dtype u_dtype, int R, void *d_Y,
+                       void *stream);
+
+/* pasta_ttv -- mode-n Tensor-Times-Vector, Algorithm 4: y(f) = sum over
+ * fiber f of val(m) * v(i_n(m)); pasta_ttm with R = 1 (d_v has dims[mode]
+ * elements, d_y nfibs). */
+pasta_status pasta_ttv(pasta_coo X, int mode, const void *d_v, pasta_dtype v_dtype, void *d_y,
+                       void *stream);
+
 #ifdef __cplusplus
 }
 #endif

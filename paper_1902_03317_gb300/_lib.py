@@ -51,6 +51,10 @@ SIGNATURES = {
     "pasta_cp_als_sweep": (_I, [_P, _P, _I, _P, _P, _P]),
     "pasta_tew_eq": (_I, [_P, _P, _I, _P, _P]),
     "pasta_ts": (_I, [_P, _I, ctypes.c_double, _P, _P]),
+    "pasta_coo_fibers": (_I, [_P, _I, _P, _P]),
+    "pasta_coo_fiber_coords": (_I, [_P, _I, _P, _P]),
+    "pasta_ttm": (_I, [_P, _I, _P, _I, _I, _P, _P]),
+    "pasta_ttv": (_I, [_P, _I, _P, _I, _P, _P]),
 }
 
 _lock = threading.Lock()

@@ -167,6 +167,57 @@ def ts(X: CooTensor, op: str, s: float, out: CooTensor | None = None) -> CooTens
     return o if o is not None else CooTensor._adopt(h, X)
 
 
+def fibers(X: CooTensor, mode: int) -> int:
+    """Build (once) the mode-``mode`` fiber table (sorting mode (mode+1) % N
+    first if needed); returns the number of fibers."""
+    X.sort_by_mode((mode + 1) % X.order)
+    n = ctypes.c_uint64()
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_coo_fibers(X.handle, int(mode), ctypes.byref(n), _stream(X.device))
+    _lib.check(st, "pasta_coo_fibers")
+    return int(n.value)
+
+
+def fiber_coords(X: CooTensor, mode: int) -> list[torch.Tensor]:
+    """The mode-``mode`` fibers' coordinates in modes mode+1, ..., mode-1
+    (cyclic): N-1 int32 tensors of nfibs."""
+    nf = fibers(X, mode)
+    out = [torch.empty(nf, dtype=torch.int32, device=X.device) for _ in range(X.order - 1)]
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_coo_fiber_coords(X.handle, int(mode), _lib.ptr_array([t.data_ptr() for t in out]),
+                                               _stream(X.device))
+    _lib.check(st, "pasta_coo_fiber_coords")
+    return out
+
+
+def ttm(X: CooTensor, U: torch.Tensor, mode: int) -> torch.Tensor:
+    """Y = X x_mode U (Algorithm 5; U is dims[mode] x R): one row per mode-n
+    fiber, in the order of ``fiber_coords``.  FP32 result (FP64 for FP64 U)."""
+    nf = fibers(X, mode)
+    if U.dim() != 2 or U.shape[0] != X.dims[mode] or not U.is_contiguous() or U.device != X.device:
+        raise ValueError(f"U must be a contiguous {X.dims[mode]} x R tensor on the tensor's device")
+    R = int(U.shape[1])
+    Y = torch.empty((nf, R), dtype=acc_dtype(U.dtype), device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_ttm(X.handle, int(mode), U.data_ptr(), pasta_dtype(U.dtype), R, Y.data_ptr(),
+                                  _stream(X.device))
+    _lib.check(st, "pasta_ttm")
+    return Y
+
+
+def ttv(X: CooTensor, v: torch.Tensor, mode: int) -> torch.Tensor:
+    """y = X x_mode v (Algorithm 4): one value per mode-n fiber."""
+    nf = fibers(X, mode)
+    if v.dim() != 1 or v.shape[0] != X.dims[mode] or not v.is_contiguous() or v.device != X.device:
+        raise ValueError(f"v must be a contiguous vector of {X.dims[mode]} on the tensor's device")
+    y = torch.empty(nf, dtype=acc_dtype(v.dtype), device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_ttv(X.handle, int(mode), v.data_ptr(), pasta_dtype(v.dtype), y.data_ptr(),
+                                  _stream(X.device))
+    _lib.check(st, "pasta_ttv")
+    return y
+
+
 def _factor_ptrs(X: CooTensor, Us: Sequence[torch.Tensor | None], skip: int = -1):
     if len(Us) != X.order:
         raise ValueError("need one factor per mode")

@@ -296,6 +296,7 @@ pasta_status pasta_coo_destroy(pasta_coo X) {
     cudaDeviceSynchronize();
     free_copy(X->orig);
     for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(X->sorted[k]);
+    for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_fibers(X->fibers[k]);
     if (X->partials) cudaFree(X->partials);
     if (X->als_normsq) cudaFree(X->als_normsq);
     if (X->scratch) cudaFree(X->scratch);
@@ -559,10 +560,12 @@ static pasta_status elementwise_output(pasta_coo X, pasta_coo Y, pasta_coo *Z, c
             return PASTA_ERR_INVALID_ARG;
         }
     bool derived = O->als_normsq != nullptr;
-    for (int k = 0; k < PASTA_MAX_ORDER; ++k) derived = derived || O->sorted[k].block != nullptr;
+    for (int k = 0; k < PASTA_MAX_ORDER; ++k)
+        derived = derived || O->sorted[k].block != nullptr || O->fibers[k].present;
     if (derived) {
         cudaStreamSynchronize(s);  // earlier work on O may still read what is freed here
         for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(O->sorted[k]);
+        for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_fibers(O->fibers[k]);
         if (O->als_normsq) {
             cudaFree(O->als_normsq);
             O->als_normsq = nullptr;
@@ -624,6 +627,59 @@ pasta_status pasta_ts(pasta_coo X, pasta_op op, double sc, pasta_coo *Z, void *s
         *Z = nullptr;
     }
     return st;
+}
+
+pasta_status pasta_coo_fibers(pasta_coo X, int mode, uint64_t *nfibs, void *stream) {
+    if (!X || mode < 0 || mode >= X->order) {
+        set_error("bad handle or mode");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    pasta_status st = build_fibers(X, mode, static_cast<cudaStream_t>(stream));
+    if (st == PASTA_OK && nfibs) *nfibs = X->fibers[mode].nfibs;
+    return st;
+}
+
+pasta_status pasta_coo_fiber_coords(pasta_coo X, int mode, uint32_t *const *d_coords, void *stream) {
+    if (!X || mode < 0 || mode >= X->order || !d_coords) {
+        set_error("bad handle, mode or d_coords");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    const pasta::FiberTable &F = X->fibers[mode];
+    if (!F.present) {
+        set_error("mode %d has no fiber table (pasta_coo_fibers)", mode);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int j = 0; j < X->order - 1; ++j) {
+        if (!d_coords[j]) continue;
+        if (F.nfibs)
+            PASTA_CUDA(cudaMemcpyAsync(d_coords[j], F.coords[j], F.nfibs * 4, cudaMemcpyDeviceToDevice, s));
+    }
+    return PASTA_OK;
+}
+
+pasta_status pasta_ttm(pasta_coo X, int mode, const void *d_U, pasta_dtype u_dtype, int R, void *d_Y,
+                       void *stream) {
+    if (!X || mode < 0 || mode >= X->order || !d_U || !ok_dtype(u_dtype) || R < 1 ||
+        R > PASTA_MAX_RANK) {
+        set_error("bad handle, mode, U, dtype or R");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (!X->fibers[mode].present) {
+        set_error("mode %d has no fiber table (pasta_coo_fibers)", mode);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    if (X->fibers[mode].nfibs == 0) return PASTA_OK;  // nothing to write; d_Y may be NULL
+    if (!d_Y) {
+        set_error("d_Y is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    return launch_ttm(X, mode, d_U, u_dtype, R, d_Y, static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_ttv(pasta_coo X, int mode, const void *d_v, pasta_dtype v_dtype, void *d_y,
+                       void *stream) {
+    return pasta_ttm(X, mode, d_v, v_dtype, 1, d_y, stream);
 }
 
 }  // extern "C"

@@ -1,0 +1,242 @@
+// Mode-n fibers and the mode-n products TTV and TTM (Sec. 3.3 and 3.4,
+// Algorithms 4 and 5).
+//
+// A mode-n fiber is the set of stored entries sharing every index but i_n.
+// In the mode-(n+1) sorted copy the key runs through modes n+1, ..., N-1,
+// 0, ..., n-1 and ends with n, so each fiber is one contiguous run there
+// (when those N-1 modes fit the key's 64 bits, checked here).  The fiber
+// table is that copy's run structure: fid[p] = the fiber of sorted position
+// p (the paper's fptr, inverted) and each fiber's N-1 coordinates.
+//
+// Built in three launches: per-tile head counts (a head is a position whose
+// fiber coordinates differ from its predecessor's), one block scanning the
+// tile counts, and a pass that ranks the heads inside each tile (warp ballots,
+// rounds of 256 positions) to write fid and the head coordinates.
+//
+// With the table, Y = X x_n U is exactly an MTTKRP of the order-2 tensor with
+// coordinates (fid, i_n) and the same values: Y(f, r) = sum_{p in f}
+// val(p) U(i_n(p), r), and fid is non-decreasing along the copy.  So TTM runs
+// the MTTKRP kernels on that two-mode view; TTV is TTM with R = 1.
+#include <algorithm>
+
+#include "pasta_internal.cuh"
+
+namespace pasta {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;
+constexpr unsigned FULL = 0xFFFFFFFFu;
+
+struct FiberView {
+    const uint32_t *idx[kMaxOrder];  // position j: mode (n + 1 + j) % N, j < N - 1
+    int nm;                          // N - 1
+    uint64_t nnz;
+};
+
+__device__ __forceinline__ bool is_head(const FiberView &v, uint64_t p) {
+    if (p == 0) return true;
+    bool h = false;
+#pragma unroll
+    for (int j = 0; j < kMaxOrder; ++j)
+        if (j < v.nm) h |= v.idx[j][p] != v.idx[j][p - 1];
+    return h;
+}
+
+// counts[t] = heads in tile t (positions t * kTile + round * 256 + thread).
+__global__ void __launch_bounds__(kThreads) k_fiber_count(FiberView v, uint32_t *counts) {
+    __shared__ uint32_t ws[kThreads / 32];
+    const uint64_t base = (uint64_t)blockIdx.x * kTile;
+    uint32_t c = 0;
+    for (int r = 0; r < kItems; ++r) {
+        const uint64_t p = base + (uint64_t)r * kThreads + threadIdx.x;
+        if (p < v.nnz && is_head(v, p)) ++c;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
+        counts[blockIdx.x] = t;
+    }
+}
+
+// Exclusive scan of counts (one block); total -> *total.
+__global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t *counts, uint32_t n, uint32_t *offsets,
+                                                      uint64_t *total) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint64_t carry;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (uint32_t b = 0; b < n; b += 1024) {
+        const uint32_t i = b + threadIdx.x;
+        const uint32_t x = i < n ? counts[i] : 0u;
+        uint32_t inc = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t s = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(FULL, s, o);
+                if (lane >= o) s += y;
+            }
+            wsum[lane] = s;
+        }
+        __syncthreads();
+        const uint64_t before = carry + (warp > 0 ? wsum[warp - 1] : 0u);
+        if (i < n) offsets[i] = (uint32_t)(before + inc - x);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[31];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *total = carry;
+}
+
+// fid[p] = (heads at or before p) - 1; each head writes its fiber's coordinates.
+__global__ void __launch_bounds__(kThreads) k_fiber_write(FiberView v, const uint32_t *offsets,
+                                                          uint32_t *fid, FiberView out_coords) {
+    __shared__ uint32_t wsum[kThreads / 32];
+    __shared__ uint32_t running;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t base = (uint64_t)blockIdx.x * kTile;
+    if (threadIdx.x == 0) running = offsets[blockIdx.x];
+    __syncthreads();
+    for (int r = 0; r < kItems; ++r) {
+        const uint64_t p = base + (uint64_t)r * kThreads + threadIdx.x;
+        const bool h = p < v.nnz && is_head(v, p);
+        const unsigned bal = __ballot_sync(FULL, h);
+        if (lane == 0) wsum[warp] = __popc(bal);
+        __syncthreads();
+        uint32_t before = running;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        const uint32_t incl = before + __popc(bal & ((2u << lane) - 1u));  // heads up to p in this round
+        if (p < v.nnz) {
+            fid[p] = incl - 1u;
+            if (h)
+                for (int j = 0; j < v.nm; ++j)
+                    const_cast<uint32_t *>(out_coords.idx[j])[incl - 1u] = v.idx[j][p];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < kThreads / 32; ++w) running += wsum[w];
+        __syncthreads();
+    }
+}
+
+int bits_for(uint64_t dim) {
+    int b = 0;
+    while (b < 64 && (dim - 1) >> b) ++b;
+    return b;
+}
+
+}  // namespace
+
+void free_fibers(FiberTable &F) {
+    if (F.block) cudaFree(F.block);
+    if (F.cblock) cudaFree(F.cblock);
+    F = FiberTable{};
+}
+
+pasta_status build_fibers(pasta_coo_s *X, int n, cudaStream_t s) {
+    FiberTable &F = X->fibers[n];
+    if (F.present) return PASTA_OK;
+    const int N = X->order;
+    const int m = (n + 1) % N;
+    const StoredCopy &c = X->sorted[m];
+    if (!c.present) {
+        set_error("mode-%d fibers need the mode-%d sorted copy (pasta_coo_sort_by_mode)", n, m);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    int bits = 0;
+    for (int k = 0; k < N; ++k)
+        if (k != n) bits += bits_for(X->dims[k]);
+    if (bits > 64) {
+        set_error("mode-%d fibers: the other modes need %d key bits (at most 64 supported)", n, bits);
+        return PASTA_ERR_UNSUPPORTED;
+    }
+    FiberView v{};
+    v.nm = N - 1;
+    v.nnz = X->nnz;
+    for (int j = 0; j < N - 1; ++j) v.idx[j] = c.idx[(n + 1 + j) % N];
+
+    const uint32_t ntiles = (uint32_t)std::max<uint64_t>(1, (X->nnz + kTile - 1) / kTile);
+    // fid (padded like a stored array, zero tail) + per-tile counts/offsets + total
+    const size_t fid_b = (size_t)X->nnz_pad * 4;
+    const size_t cnt_b = ((size_t)ntiles * 4 + 255) & ~(size_t)255;
+    char *blk = nullptr;
+    cudaError_t e = cudaMalloc((void **)&blk, fid_b + 2 * cnt_b + 256);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc for the mode-%d fiber table failed", n);
+        return PASTA_ERR_NOMEM;
+    }
+    F.block = blk;
+    F.fid = reinterpret_cast<uint32_t *>(blk);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(blk + fid_b);
+    uint32_t *offsets = reinterpret_cast<uint32_t *>(blk + fid_b + cnt_b);
+    uint64_t *total = reinterpret_cast<uint64_t *>(blk + fid_b + 2 * cnt_b);
+    uint64_t nfibs = 0;
+    e = cudaMemsetAsync(F.fid, 0, fid_b, s);
+    if (e == cudaSuccess && X->nnz > 0) {
+        k_fiber_count<<<ntiles, kThreads, 0, s>>>(v, counts);
+        k_scan_counts<<<1, 1024, 0, s>>>(counts, ntiles, offsets, total);
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&nfibs, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e == cudaSuccess && nfibs > 0) {
+        const size_t per = ((size_t)nfibs * 4 + 255) & ~(size_t)255;
+        e = cudaMalloc(&F.cblock, per * (size_t)(N - 1));
+        if (e == cudaSuccess) {
+            FiberView out{};
+            out.nm = N - 1;
+            for (int j = 0; j < N - 1; ++j) {
+                F.coords[j] = reinterpret_cast<uint32_t *>(static_cast<char *>(F.cblock) + per * j);
+                out.idx[j] = F.coords[j];
+            }
+            k_fiber_write<<<ntiles, kThreads, 0, s>>>(v, offsets, F.fid, out);
+            e = cudaGetLastError();
+        }
+    }
+    if (e != cudaSuccess) {
+        pasta_status st = cuda_fail(e, "fiber table");
+        cudaStreamSynchronize(s);
+        free_fibers(F);
+        return st;
+    }
+    F.nfibs = nfibs;
+    F.present = true;
+    return PASTA_OK;
+}
+
+pasta_status launch_ttm(pasta_coo_s *X, int n, const void *U, pasta_dtype dt, int R, void *Y,
+                        cudaStream_t s) {
+    const FiberTable &F = X->fibers[n];
+    const int m = (n + 1) % X->order;
+    const StoredCopy &c = X->sorted[m];
+    // the order-2 view (fiber, i_n) of the mode-(n+1) sorted copy
+    pasta_coo_s V;
+    V.order = 2;
+    V.dims[0] = F.nfibs;
+    V.dims[1] = X->dims[n];
+    V.nnz = X->nnz;
+    V.nnz_pad = X->nnz_pad;
+    V.device = X->device;
+    V.num_sms = X->num_sms;
+    StoredCopy vc;
+    vc.idx[0] = F.fid;
+    vc.idx[1] = c.idx[n];
+    vc.val = c.val;
+    vc.present = true;
+    const void *Us[2] = {nullptr, U};
+    return launch_mttkrp(&V, vc, Us, dt, 0, R, Y, s);
+}
+
+}  // namespace pasta

@@ -249,7 +249,7 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 
 pasta_status launch_mttkrp(const pasta_coo_s *X, const StoredCopy &c, const void *const *U,
                            pasta_dtype dt, int mode, int R, void *M, cudaStream_t s) {
-    if (stream_supported(dt, X->order, R, U, mode, M)) {
+    if (stream_supported(dt, X->order, R, U, mode, M, 2)) {
         PASTA_CUDA(cudaMemsetAsync(M, 0, (size_t)X->dims[mode] * (size_t)R * sizeof(float), s));
         if (X->nnz == 0) return PASTA_OK;
         StreamLaunch l;

@@ -40,6 +40,18 @@ struct StoredCopy {
     bool present = false;
 };
 
+// Mode-n fibers (the preprocessing of Algorithms 4 and 5): the stored
+// entries that share every index but i_n.  They are contiguous in the
+// mode-(n+1) sorted copy, whose key ends with mode n.
+struct FiberTable {
+    uint64_t nfibs = 0;
+    uint32_t *fid = nullptr;             // per entry of that copy: its fiber (padded to nnz_pad)
+    uint32_t *coords[kMaxOrder] = {};    // nfibs each: indices in modes n+1, ..., n-1 (cyclic)
+    void *block = nullptr;               // fid
+    void *cblock = nullptr;              // coords
+    bool present = false;
+};
+
 }  // namespace pasta
 
 struct pasta_coo_s {
@@ -56,6 +68,7 @@ struct pasta_coo_s {
     double *als_normsq = nullptr;  // CP-ALS: sum of squared values (device), computed once
     void *scratch = nullptr;       // grow-only scratch (handle_scratch)
     size_t scratch_bytes = 0;
+    pasta::FiberTable fibers[PASTA_MAX_ORDER];  // per mode, built by pasta_coo_fibers
 };
 
 namespace pasta {
@@ -126,9 +139,10 @@ struct StreamLaunch {
     int max_blocks = 0;          // 0 = no cap
     int *blocks_used = nullptr;  // optional
 };
-// True when the streaming kernels cover this case (see stream.cu).
+// True when the streaming kernels cover this case (see stream.cu); the loss
+// kinds need order >= 3, MTTKRP (min_order 2) also takes order 2.
 bool stream_supported(pasta_dtype dt, int order, int R, const void *const *U, int skip,
-                      const void *out);
+                      const void *out, int min_order = 3);
 // kind: 0 MTTKRP, 1 loss forward, 2 loss backward (one mode)
 pasta_status launch_stream(int kind, const StreamLaunch &l, cudaStream_t s);
 
@@ -162,6 +176,12 @@ pasta_status same_coordinates(const pasta_coo_s *X, const pasta_coo_s *Y, cudaSt
                               bool *same);
 pasta_status launch_elementwise(const float *x, const float *y, double s, float *z, uint64_t n_pad,
                                 int op, int num_sms, cudaStream_t stream);
+
+// Fiber tables and mode-n products (fibers.cu).
+pasta_status build_fibers(pasta_coo_s *X, int mode, cudaStream_t stream);
+void free_fibers(pasta::FiberTable &F);
+pasta_status launch_ttm(pasta_coo_s *X, int mode, const void *U, pasta_dtype dt, int R, void *Y,
+                        cudaStream_t stream);
 
 pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,
                             uint64_t n, const double *scale, cudaStream_t stream);

@@ -3,7 +3,7 @@
 // dispatch to the per-kind launchers (stream_mttkrp.cu, stream_loss_fwd.cu,
 // stream_loss_bwd.cu).
 //
-// Covered: FP32/BF16/FP16 factors, order 3..5, 16-byte aligned factors and
+// Covered: FP32/BF16/FP16 factors, order 3..5 (2..5 for MTTKRP), 16-byte aligned factors and
 // outputs, and R * sizeof(element) = 16 * L with L a power of two <= 32 (so
 // the L lanes of a group cover a row exactly).  Anything else returns
 // PASTA_ERR_UNSUPPORTED and the caller uses the general kernels.
@@ -17,9 +17,9 @@ bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) ==
 }  // namespace
 
 bool stream_supported(pasta_dtype dt, int order, int R, const void *const *U, int skip,
-                      const void *out) {
+                      const void *out, int min_order) {
     if (dt != PASTA_F32 && dt != PASTA_BF16 && dt != PASTA_F16) return false;
-    if (order < 3 || order > 5) return false;
+    if (order < min_order || order > 5) return false;
     const int bytes = R * (int)dtype_size(dt);
     if (bytes % 16 != 0) return false;
     const int L = bytes / 16;

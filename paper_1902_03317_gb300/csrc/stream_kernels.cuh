@@ -203,7 +203,13 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
         if (changed) s.cur = iw[0][q];
         if (!MT && need0[q]) s.row0 = rows[q][0];
         float p[VEC], r[VEC];
-        if (KIND == kMttkrp) {
+        if constexpr (KIND == kMttkrp && NR == 1) {  // order 2: val times one row
+            widen<T, VEC>(rows[q][0], r);
+            if (ok) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) s.acc[e] = fmaf(vw[q], r[e], s.acc[e]);
+            }
+        } else if (KIND == kMttkrp) {
             widen<T, VEC>(rows[q][0], r);
 #pragma unroll
             for (int e = 0; e < VEC; ++e) p[e] = vw[q] * r[e];

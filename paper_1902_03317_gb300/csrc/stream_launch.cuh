@@ -25,6 +25,7 @@ constexpr int kStages = 2;
 // not for the backward; higher orders need two blocks' budget.
 template <typename T, int N, int KIND>
 constexpr int min_blocks() {
+    if (N == 2) return 4;
     if (N != 3) return 2;
     if (KIND == stream::kLossBwd) return 3;  // the backward spills too much at 4
     return sizeof(T) == 4 ? 4 : 3;
@@ -90,6 +91,9 @@ pasta_status by_lanes(const StreamLaunch &l, cudaStream_t s) {
 template <typename T, int KIND>
 pasta_status by_order(const StreamLaunch &l, cudaStream_t s) {
     switch (l.order) {
+        case 2:  // MTTKRP only (TTM/TTV run as an order-2 MTTKRP)
+            if constexpr (KIND == stream::kMttkrp) return by_lanes<T, 2, KIND>(l, s);
+            return PASTA_ERR_UNSUPPORTED;
         case 3: return by_lanes<T, 3, KIND>(l, s);
         case 4: return by_lanes<T, 4, KIND>(l, s);
         case 5: return by_lanes<T, 5, KIND>(l, s);

@@ -162,3 +162,38 @@ def test_zipf3d_100M_tew_eq_and_ts_sampled():
     for t in (X, Y, Z):
         t.close()
     torch.cuda.empty_cache()
+
+
+def test_zipf3d_100M_ttm_sampled_fibers():
+    """Mode-1 TTM (R = 32, FP32) of the full tensor: fiber count against the
+    distinct (i_2, i_0) pairs, and sampled fibers (the heaviest and random
+    ones) against the oracle run on the entries of those fibers."""
+    wl = synth.WORKLOADS["zipf3d"]
+    Xd = synth.generate(wl, device=G.DEV)
+    X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
+    n = 1
+    key = (Xd.idx[2].to(torch.int64) * wl.dims[0] + Xd.idx[0].to(torch.int64))
+    uniq, counts = torch.unique(key, return_counts=True)
+    idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
+    val = Xd.val.cpu().numpy().astype(np.float64)
+    del Xd
+    U = torch.randn(wl.dims[n], 32, device=G.DEV)
+    Y = pasta.ttm(X, U, n)
+    assert Y.shape[0] == uniq.numel()
+    coords = pasta.fiber_coords(X, n)  # modes 2, 0
+    fkey = coords[0].to(torch.int64) * wl.dims[0] + coords[1].to(torch.int64)
+    assert torch.equal(fkey, uniq)  # sorted, distinct, complete
+    rng = np.random.default_rng(4)
+    pick = [int(torch.argmax(counts))] + [int(x) for x in rng.choice(uniq.numel(), 8, replace=False)]
+    pkeys = fkey[pick].cpu().numpy()
+    keys_h = key.cpu().numpy()
+    keep = np.isin(keys_h, pkeys)
+    sidx = [ix[keep] for ix in idx]
+    c_ref, y_ref = oracle.ttm(wl.dims, sidx, val[keep], U.double().cpu().numpy(), n)
+    ref_keys = c_ref[0].astype(np.int64) * wl.dims[0] + c_ref[1].astype(np.int64)
+    order = np.argsort(pkeys)
+    assert np.array_equal(ref_keys, pkeys[order])
+    got = Y[torch.tensor(np.array(pick)[order], device=G.DEV)].cpu().numpy()
+    assert G.rel_err(got, y_ref) < G.FP32_TOL
+    X.close()
+    torch.cuda.empty_cache()
