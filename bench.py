@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--no-loss-compare", action="store_true")
     ap.add_argument("--no-als", action="store_true")
     ap.add_argument("--no-tew", action="store_true")
+    ap.add_argument("--no-ttm", action="store_true")
     ap.add_argument("--factor-dtype", default="f32", choices=["f32", "bf16", "f16"],
                     help="factor storage type of the timed step (FP32 accumulation either way)")
     ap.add_argument("--nnz", type=float, default=None,
@@ -317,6 +318,8 @@ def run_own(args, rank, world, local):
     del Xd
     torch.cuda.empty_cache()
 
+    if not args.no_ttm and rank == 0:
+        result["ttm_ttv"] = ttm_timing(pasta, X, wl, peak, args)
     if not args.no_tew and rank == 0:
         result["tew_ts"] = tew_ts_timing(pasta, X, N, nnz, peak, args)
     if not args.no_als and rank == 0 and args.factor_dtype == "f32":
@@ -402,6 +405,44 @@ def tew_ts_timing(pasta, X, N, nnz, peak, args):
                      "achieved_gbs": round(gbs, 1), "frac": round(gbs / peak, 4), "calls_timed": K}
     Y.close()
     Z.close()
+    return out
+
+
+def ttm_timing(pasta, X, wl, peak, args):
+    """Mode-n fiber tables (preprocessing, timed once) and TTM (R = 32, FP32)
+    / TTV on the benchmark tensor, every mode, CUDA events.  Compulsory bytes
+    of one TTM: the view's stream (fiber id, i_n and value: 12 B per entry),
+    U's touched rows and the nfibs x R output; TTV the same with R = 1."""
+    import torch
+    out = {}
+    K = max(3, args.steps // 3)
+    for n in range(wl.order):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        nf = pasta.fibers(X, n)
+        e1.record()
+        torch.cuda.synchronize()
+        fib_ms = e0.elapsed_time(e1)
+        U = torch.randn(wl.dims[n], 32, device=X.device)
+        v = torch.randn(wl.dims[n], device=X.device)
+        rows = min(wl.dims[n], wl.nnz)  # upper bound on touched rows
+        res = {"nfibs": nf, "fiber_table_ms": round(fib_ms, 3)}
+        for name, call, R in (("ttm_r32", lambda: pasta.ttm(X, U, n), 32), ("ttv", lambda: pasta.ttv(X, v, n), 1)):
+            call()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(K):
+                call()
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / K
+            alg = wl.nnz * 12 + rows * R * 4 + nf * R * 4
+            gbs = alg / (ms * 1e-3) / 1e9
+            res[name] = {"ms": round(ms, 4), "alg_bytes": alg, "achieved_gbs": round(gbs, 1),
+                         "frac": round(gbs / peak, 4)}
+        out[f"mode{n}"] = res
     return out
 
 

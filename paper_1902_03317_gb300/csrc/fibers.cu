@@ -16,7 +16,9 @@
 // With the table, Y = X x_n U is exactly an MTTKRP of the order-2 tensor with
 // coordinates (fid, i_n) and the same values: Y(f, r) = sum_{p in f}
 // val(p) U(i_n(p), r), and fid is non-decreasing along the copy.  So TTM runs
-// the MTTKRP kernels on that two-mode view; TTV is TTM with R = 1.
+// the MTTKRP kernels on that two-mode view.  TTV (R = 1) has its own kernel
+// (k_ttv): with one value per entry the MTTKRP lane layout idles, and fibers
+// are short, so a warp-wide segmented scan per 32 entries does the work.
 #include <algorithm>
 
 #include "pasta_internal.cuh"
@@ -130,6 +132,76 @@ __global__ void __launch_bounds__(kThreads) k_fiber_write(FiberView v, const uin
     }
 }
 
+// TTV: y(f) = sum over fiber f of val * v(i_n).  Each warp takes a chunk of
+// kTtvChunk consecutive entries in rounds of 32; per round a segmented
+// inclusive scan over lanes (fiber ids are non-decreasing) sums each
+// fiber's entries, the fiber still open at lane 31 is carried into the next
+// round, and a finished fiber is stored plainly if it lies wholly inside the
+// chunk, else added atomically (the chunk's first and last fibers may be
+// shared with the neighbouring chunks).  y must be zero-filled.
+constexpr int kTtvChunk = 1024;
+
+template <typename T, typename A>
+__global__ void __launch_bounds__(256) k_ttv(const uint32_t *fid, const uint32_t *in, const float *val,
+                                             const T *v, A *y, uint64_t nnz) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t c0 = warp * kTtvChunk;
+    if (c0 >= nnz) return;
+    const uint64_t c1 = min(nnz, c0 + kTtvChunk);
+    uint32_t carry_f = kNoRow;
+    A carry_t = 0;
+    bool carry_first = true;  // the carried fiber began at the chunk's first entry
+    for (uint64_t r0 = c0; r0 < c1; r0 += 32) {
+        const uint64_t p = r0 + lane;
+        const bool ok = p < c1;
+        const uint32_t f = ok ? fid[p] : kNoRow;
+        A t = ok ? (A)val[p] * (A)v[in[p]] : (A)0;
+        const bool cont = (lane == 0) && f == carry_f;  // continues the carried fiber
+        if (carry_f != kNoRow) {  // warp-uniform
+            // the carried fiber ended with the previous round: write it
+            const uint32_t f0 = __shfl_sync(FULL, f, 0);
+            if (lane == 0 && f0 != carry_f) {
+                if (carry_first)
+                    atomicAdd(&y[carry_f], carry_t);
+                else
+                    y[carry_f] = carry_t;
+            }
+        }
+        if (cont) t += carry_t;
+        // segmented inclusive scan over lanes with equal fiber id
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const A tp = __shfl_up_sync(FULL, t, o);
+            const uint32_t fp = __shfl_up_sync(FULL, f, o);
+            if (lane >= o && fp == f) t += tp;
+        }
+        // every lane takes part in each shuffle and ballot (none is short-circuited)
+        const uint32_t fnext = __shfl_down_sync(FULL, f, 1);
+        const uint32_t fprev = __shfl_up_sync(FULL, f, 1);
+        const bool cont0 = __shfl_sync(FULL, (int)cont, 0) != 0;
+        const bool last_in_round = ok && (lane == 31 || fnext != f || r0 + lane + 1 >= c1);
+        // first lane of this lane's segment within the round
+        const unsigned starts = __ballot_sync(FULL, ok && (lane == 0 || fprev != f));
+        const int seg0 = 31 - __clz(starts & ((2u << lane) - 1u));
+        const bool seg_from_carry = (seg0 == 0) && cont0;
+        const bool seg_first = (r0 == c0 && seg0 == 0) || (seg_from_carry && carry_first);
+        const bool open = last_in_round && lane == 31 && r0 + 32 < c1;  // may continue next round
+        if (last_in_round && !open) {
+            const bool chunk_last = (p + 1 == c1);  // may continue in the next chunk
+            if (seg_first || chunk_last)
+                atomicAdd(&y[f], t);
+            else
+                y[f] = t;
+        }
+        // carry the fiber open at lane 31 into the next round
+        carry_f = __shfl_sync(FULL, open ? f : kNoRow, 31);
+        carry_t = __shfl_sync(FULL, t, 31);
+        const bool first31 = __shfl_sync(FULL, (int)seg_first, 31) != 0;
+        carry_first = (carry_f != kNoRow) && first31;
+    }
+}
+
 int bits_for(uint64_t dim) {
     int b = 0;
     while (b < 64 && (dim - 1) >> b) ++b;
@@ -221,6 +293,33 @@ pasta_status launch_ttm(pasta_coo_s *X, int n, const void *U, pasta_dtype dt, in
     const FiberTable &F = X->fibers[n];
     const int m = (n + 1) % X->order;
     const StoredCopy &c = X->sorted[m];
+    if (R == 1) {  // TTV
+        const size_t acc = dt == PASTA_F64 ? 8 : 4;
+        PASTA_CUDA(cudaMemsetAsync(Y, 0, F.nfibs * acc, s));
+        if (X->nnz == 0) return PASTA_OK;
+        const uint64_t warps = (X->nnz + kTtvChunk - 1) / kTtvChunk;
+        const int blocks = (int)((warps + 7) / 8);
+        switch (dt) {
+            case PASTA_F32:
+                k_ttv<float, float><<<blocks, 256, 0, s>>>(F.fid, c.idx[n], c.val, static_cast<const float *>(U),
+                                                            static_cast<float *>(Y), X->nnz);
+                break;
+            case PASTA_BF16:
+                k_ttv<__nv_bfloat16, float><<<blocks, 256, 0, s>>>(
+                    F.fid, c.idx[n], c.val, static_cast<const __nv_bfloat16 *>(U), static_cast<float *>(Y), X->nnz);
+                break;
+            case PASTA_F16:
+                k_ttv<__half, float><<<blocks, 256, 0, s>>>(F.fid, c.idx[n], c.val, static_cast<const __half *>(U),
+                                                             static_cast<float *>(Y), X->nnz);
+                break;
+            case PASTA_F64:
+                k_ttv<double, double><<<blocks, 256, 0, s>>>(F.fid, c.idx[n], c.val, static_cast<const double *>(U),
+                                                              static_cast<double *>(Y), X->nnz);
+                break;
+        }
+        PASTA_CUDA(cudaGetLastError());
+        return PASTA_OK;
+    }
     // the order-2 view (fiber, i_n) of the mode-(n+1) sorted copy
     pasta_coo_s V;
     V.order = 2;

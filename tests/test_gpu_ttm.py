@@ -53,15 +53,17 @@ def test_fibers_and_ttm_match_oracle(name, nnz, dims):
     X.close()
 
 
-@pytest.mark.parametrize("name,nnz,dims", CASES[:2])
+@pytest.mark.parametrize("name,nnz,dims", CASES)
 def test_ttv_matches_oracle(name, nnz, dims):
     wl, X, idx, val = _tensor(name, nnz, dims)
     for n in range(wl.order):
-        v = torch.randn(wl.dims[n], dtype=torch.float32, device=G.DEV)
-        y = pasta.ttv(X, v, n)
-        coords, ref = oracle.ttv(wl.dims, idx, val, v.double().cpu().numpy(), n)
-        assert G.rel_err(y.cpu().numpy(), ref) < G.FP32_TOL
-        assert pasta.fibers(X, n) == ref.shape[0]
+        for dtype in (torch.float32, torch.bfloat16, torch.float64):
+            v = torch.randn(wl.dims[n], dtype=torch.float64, device=G.DEV).to(dtype)
+            y = pasta.ttv(X, v, n)
+            coords, ref = oracle.ttv(wl.dims, idx, val, v.double().cpu().numpy(), n)
+            tol = 1e-12 if dtype == torch.float64 else G.FP32_TOL
+            assert G.rel_err(y.cpu().numpy(), ref) < tol, (name, n, dtype)
+            assert pasta.fibers(X, n) == ref.shape[0]
     X.close()
 
 
