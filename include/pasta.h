@@ -40,6 +40,7 @@
 #ifndef PASTA_H
 #define PASTA_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -388,6 +389,22 @@ pasta_status pasta_ttm(pasta_coo X, int mode, const void *d_U, pasta_dtype u_dty
  * elements, d_y nfibs). */
 pasta_status pasta_ttv(pasta_coo X, int mode, const void *d_v, pasta_dtype v_dtype, void *d_y,
                        void *stream);
+
+/*
+ * Device memory of the library's own buffers (stored copies, scratch, fiber
+ * tables, partial sums).  By default cudaMalloc/cudaFree; a caller with its
+ * own caching allocator (a framework's) can route them through it, so that
+ * handles created and destroyed in a loop reuse memory instead of mapping it
+ * anew.  alloc returns NULL on failure (the call then fails with
+ * PASTA_ERR_NOMEM); blocks must be at least 256-byte aligned.  The library
+ * synchronises the device before it frees a block that kernels may still
+ * use.  Both NULL restores the default.  Refused (PASTA_ERR_INVALID_ARG)
+ * while any block from the current allocator is still held.  The paper has
+ * no counterpart.
+ */
+typedef void *(*pasta_alloc_fn)(size_t bytes, int device, void *stream, void *ctx);
+typedef void (*pasta_free_fn)(void *ptr, void *ctx);
+pasta_status pasta_set_allocator(pasta_alloc_fn alloc, pasta_free_fn free_fn, void *ctx);
 
 #ifdef __cplusplus
 }

@@ -8,9 +8,9 @@ library is missing, calls fail with a RuntimeError.
 """
 from .api import (CooTensor, CPLoss, acc_dtype, convert, cp_als, cp_als_sweep, cp_loss,  # noqa: F401
                   cp_loss_bwd, cp_loss_fwd, cp_loss_fwd_bwd, fiber_coords, fibers, mttkrp, tew_eq,
-                  ts, ttm, ttv)
+                  ts, ttm, ttv, use_torch_allocator)
 from ._lib import PastaError  # noqa: F401
 
 __all__ = ["CooTensor", "CPLoss", "cp_loss", "cp_loss_fwd", "cp_loss_bwd", "cp_loss_fwd_bwd", "mttkrp",
            "cp_als_sweep", "cp_als", "tew_eq", "ts", "fibers", "fiber_coords", "ttm", "ttv", "convert",
-           "acc_dtype", "PastaError"]
+           "acc_dtype", "use_torch_allocator", "PastaError"]

@@ -55,6 +55,7 @@ SIGNATURES = {
     "pasta_coo_fiber_coords": (_I, [_P, _I, _P, _P]),
     "pasta_ttm": (_I, [_P, _I, _P, _I, _I, _P, _P]),
     "pasta_ttv": (_I, [_P, _I, _P, _I, _P, _P]),
+    "pasta_set_allocator": (_I, [_P, _P, _P]),
 }
 
 _lock = threading.Lock()

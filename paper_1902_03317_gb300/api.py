@@ -40,6 +40,48 @@ def _stream(device) -> int:
     return torch.cuda.current_stream(device).cuda_stream
 
 
+# The library's own device buffers (stored copies, scratch, fiber tables) go
+# through torch's caching allocator (pasta_set_allocator), so handles built
+# and dropped in a loop reuse memory and torch's memory accounting sees them.
+_ALLOC_T = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_T = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def _torch_alloc(nbytes, device, stream, ctx):
+    try:
+        return torch.cuda.caching_allocator_alloc(int(nbytes), int(device), int(stream or 0))
+    except Exception:  # out of memory: the library reports PASTA_ERR_NOMEM
+        return None
+
+
+def _torch_free(ptr, ctx):
+    torch.cuda.caching_allocator_delete(int(ptr))
+
+
+_TORCH_CALLBACKS = (_ALLOC_T(_torch_alloc), _FREE_T(_torch_free))
+_allocator = None  # None until the first handle; then "torch" or "cuda"
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route the library's device buffers through torch's caching allocator
+    (the default from the first handle on) or back to cudaMalloc.  Only
+    possible while no library buffer is held."""
+    global _allocator
+    L = _lib.lib()
+    if enable:
+        st = L.pasta_set_allocator(ctypes.cast(_TORCH_CALLBACKS[0], ctypes.c_void_p),
+                                   ctypes.cast(_TORCH_CALLBACKS[1], ctypes.c_void_p), None)
+    else:
+        st = L.pasta_set_allocator(None, None, None)
+    _lib.check(st, "pasta_set_allocator")
+    _allocator = "torch" if enable else "cuda"
+
+
+def _ensure_allocator() -> None:
+    if _allocator is None:
+        use_torch_allocator(True)
+
+
 class CooTensor:
     """A COO tensor held by libpasta on one CUDA device (``pasta_coo``).
 
@@ -70,6 +112,7 @@ class CooTensor:
         val_c = val.contiguous()
         if val_c.dtype != torch.float32:
             raise TypeError("values must be float32")
+        _ensure_allocator()
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = _lib.lib().pasta_coo_create(

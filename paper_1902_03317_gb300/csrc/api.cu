@@ -6,6 +6,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <new>
 
 #include "pasta_internal.cuh"
@@ -29,18 +31,81 @@ pasta_status cuda_fail(cudaError_t e, const char *where) {
     return e == cudaErrorMemoryAllocation ? PASTA_ERR_NOMEM : PASTA_ERR_CUDA;
 }
 
+// Device buffers: cudaMalloc/cudaFree unless the caller installed an
+// allocator (pasta_set_allocator).  The number of live blocks guards against
+// swapping allocators while blocks of the old one are held.
+namespace {
+std::mutex g_alloc_mu;
+pasta_alloc_fn g_alloc = nullptr;
+pasta_free_fn g_free = nullptr;
+void *g_alloc_ctx = nullptr;
+std::atomic<long long> g_live{0};
+}  // namespace
+
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t s) {
+    pasta_alloc_fn a;
+    void *ctx;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        a = g_alloc;
+        ctx = g_alloc_ctx;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!a) {
+        e = cudaMalloc(p, bytes);
+    } else {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) {
+            *p = a(bytes, dev, static_cast<void *>(s), ctx);
+            if (!*p) e = cudaErrorMemoryAllocation;
+            else if ((reinterpret_cast<uintptr_t>(*p) & 255u) != 0) {
+                pasta_free_fn f;
+                {
+                    std::lock_guard<std::mutex> lock(g_alloc_mu);
+                    f = g_free;
+                }
+                if (f) f(*p, ctx);
+                *p = nullptr;
+                e = cudaErrorMisalignedAddress;
+            }
+        }
+    }
+    if (e == cudaSuccess) ++g_live;
+    return e;
+}
+
+void dev_free(void *p) {
+    if (!p) return;
+    pasta_free_fn f;
+    void *ctx;
+    {
+        std::lock_guard<std::mutex> lock(g_alloc_mu);
+        f = g_free;
+        ctx = g_alloc_ctx;
+    }
+    if (f)
+        f(p, ctx);
+    else
+        cudaFree(p);
+    --g_live;
+}
+
 // Scratch of one handle (sort keys and histograms, CP-ALS buffers): one
 // plain device allocation that only grows, kept until pasta_coo_destroy, so
 // successive sorts and sweeps on a handle reuse it.  Growing it waits for the
-// device, as cudaFree does.  Calls on one handle are stream-ordered, so its
-// users never overlap.
+// device.  Calls on one handle are stream-ordered, so its users never
+// overlap.
 pasta_status handle_scratch(pasta_coo_s *X, size_t bytes, void **out) {
     if (bytes > X->scratch_bytes) {
-        if (X->scratch) cudaFree(X->scratch);
+        if (X->scratch) {
+            cudaDeviceSynchronize();  // kernels may still use the old buffer
+            dev_free(X->scratch);
+        }
         X->scratch = nullptr;
         X->scratch_bytes = 0;
         const size_t grow = (bytes + ((size_t)1 << 20) - 1) & ~(((size_t)1 << 20) - 1);
-        cudaError_t e = cudaMalloc(&X->scratch, grow);
+        cudaError_t e = dev_malloc(&X->scratch, grow, 0);
         if (e != cudaSuccess) {
             X->scratch = nullptr;
             cudaGetLastError();
@@ -97,7 +162,7 @@ pasta_status alloc_copy(pasta_coo_s *X, StoredCopy &c, bool with_perm) {
     const size_t arr = (size_t)X->nnz_pad * 4;  // multiple of 4096 bytes
     const int narr = X->order + 1 + (with_perm ? 1 : 0);
     void *block = nullptr;
-    cudaError_t e = cudaMalloc(&block, arr * (size_t)narr);
+    cudaError_t e = dev_malloc(&block, arr * (size_t)narr, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc of %zu bytes for a stored copy failed", arr * (size_t)narr);
@@ -113,7 +178,7 @@ pasta_status alloc_copy(pasta_coo_s *X, StoredCopy &c, bool with_perm) {
 }
 
 void free_copy(StoredCopy &c) {
-    if (c.block) cudaFree(c.block);
+    if (c.block) dev_free(c.block);
     c = StoredCopy{};
 }
 
@@ -218,8 +283,8 @@ pasta_status make_handle(pasta_coo *out, int order, const uint64_t *dims, uint64
     if (e != cudaSuccess) st = cuda_fail(e, "device query");
     if (st == PASTA_OK) st = alloc_copy(X, X->orig, false);
     if (st == PASTA_OK) {
-        e = cudaMalloc(&X->partials, kPartialsCap * sizeof(double));
-        if (e != cudaSuccess) st = cuda_fail(e, "cudaMalloc(partials)");
+        e = dev_malloc(reinterpret_cast<void **>(&X->partials), kPartialsCap * sizeof(double), s);
+        if (e != cudaSuccess) st = cuda_fail(e, "allocation of partials");
         X->partials_cap = kPartialsCap;
     }
     if (st == PASTA_OK) {
@@ -297,9 +362,9 @@ pasta_status pasta_coo_destroy(pasta_coo X) {
     free_copy(X->orig);
     for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(X->sorted[k]);
     for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_fibers(X->fibers[k]);
-    if (X->partials) cudaFree(X->partials);
-    if (X->als_normsq) cudaFree(X->als_normsq);
-    if (X->scratch) cudaFree(X->scratch);
+    dev_free(X->partials);
+    dev_free(X->als_normsq);
+    dev_free(X->scratch);
     delete X;
     return PASTA_OK;
 }
@@ -567,7 +632,7 @@ static pasta_status elementwise_output(pasta_coo X, pasta_coo Y, pasta_coo *Z, c
         for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(O->sorted[k]);
         for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_fibers(O->fibers[k]);
         if (O->als_normsq) {
-            cudaFree(O->als_normsq);
+            dev_free(O->als_normsq);
             O->als_normsq = nullptr;
         }
     }
@@ -680,6 +745,23 @@ pasta_status pasta_ttm(pasta_coo X, int mode, const void *d_U, pasta_dtype u_dty
 pasta_status pasta_ttv(pasta_coo X, int mode, const void *d_v, pasta_dtype v_dtype, void *d_y,
                        void *stream) {
     return pasta_ttm(X, mode, d_v, v_dtype, 1, d_y, stream);
+}
+
+pasta_status pasta_set_allocator(pasta_alloc_fn alloc, pasta_free_fn free_fn, void *ctx) {
+    if ((alloc == nullptr) != (free_fn == nullptr)) {
+        set_error("give both alloc and free, or neither");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    std::lock_guard<std::mutex> lock(pasta::g_alloc_mu);
+    if (pasta::g_live.load() != 0) {
+        set_error("%lld library blocks are still held; destroy the handles first",
+                  (long long)pasta::g_live.load());
+        return PASTA_ERR_INVALID_ARG;
+    }
+    pasta::g_alloc = alloc;
+    pasta::g_free = free_fn;
+    pasta::g_alloc_ctx = ctx;
+    return PASTA_OK;
 }
 
 }  // extern "C"

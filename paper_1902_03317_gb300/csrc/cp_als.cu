@@ -500,10 +500,10 @@ pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *la
 
     // ||X||^2 once per handle (the values never change after create)
     if (!X->als_normsq) {
-        e = cudaMalloc(&X->als_normsq, sizeof(double));
+        e = dev_malloc(reinterpret_cast<void **>(&X->als_normsq), sizeof(double), s);
         if (e != cudaSuccess) {
             X->als_normsq = nullptr;
-            return fail(cuda_fail(e, "cudaMalloc(normsq)"));
+            return fail(cuda_fail(e, "allocation of normsq"));
         }
         const int b = (int)std::max<uint64_t>(1, std::min<uint64_t>((X->nnz + 255) / 256, (uint64_t)nblk));
         k_sumsq<<<b, 256, 0, s>>>(X->orig.val, X->nnz, part);

@@ -211,8 +211,8 @@ int bits_for(uint64_t dim) {
 }  // namespace
 
 void free_fibers(FiberTable &F) {
-    if (F.block) cudaFree(F.block);
-    if (F.cblock) cudaFree(F.cblock);
+    dev_free(F.block);
+    dev_free(F.cblock);
     F = FiberTable{};
 }
 
@@ -243,7 +243,7 @@ pasta_status build_fibers(pasta_coo_s *X, int n, cudaStream_t s) {
     const size_t fid_b = (size_t)X->nnz_pad * 4;
     const size_t cnt_b = ((size_t)ntiles * 4 + 255) & ~(size_t)255;
     char *blk = nullptr;
-    cudaError_t e = cudaMalloc((void **)&blk, fid_b + 2 * cnt_b + 256);
+    cudaError_t e = dev_malloc((void **)&blk, fid_b + 2 * cnt_b + 256, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("cudaMalloc for the mode-%d fiber table failed", n);
@@ -265,7 +265,7 @@ pasta_status build_fibers(pasta_coo_s *X, int n, cudaStream_t s) {
     }
     if (e == cudaSuccess && nfibs > 0) {
         const size_t per = ((size_t)nfibs * 4 + 255) & ~(size_t)255;
-        e = cudaMalloc(&F.cblock, per * (size_t)(N - 1));
+        e = dev_malloc(&F.cblock, per * (size_t)(N - 1), s);
         if (e == cudaSuccess) {
             FiberView out{};
             out.nm = N - 1;

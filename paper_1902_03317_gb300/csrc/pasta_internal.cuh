@@ -22,6 +22,10 @@ constexpr uint64_t kPadEntries = 1024;    // stored arrays are padded to this mu
 void set_error(const char *fmt, ...);
 pasta_status cuda_fail(cudaError_t e, const char *where);
 
+// The library's device buffers go through these (pasta_set_allocator).
+cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t stream);
+void dev_free(void *p);
+
 #define PASTA_CUDA(call)                                         \
     do {                                                         \
         cudaError_t e_ = (call);                                 \

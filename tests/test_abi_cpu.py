@@ -74,3 +74,19 @@ def test_product_path_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="not built"):
         _lib.lib()
+
+
+def test_set_allocator_argument_checks():
+    """Both callbacks or neither; resetting to the default always works when
+    no block is held (no GPU needed: nothing is allocated)."""
+    import ctypes
+    from paper_1902_03317_gb300 import _lib
+    L = _lib.lib()
+    ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p)
+    FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+    a = ALLOC(lambda n, d, s, c: None)
+    f = FREE(lambda p, c: None)
+    assert L.pasta_set_allocator(ctypes.cast(a, ctypes.c_void_p), None, None) == 1
+    assert L.pasta_set_allocator(None, ctypes.cast(f, ctypes.c_void_p), None) == 1
+    assert L.pasta_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None) == 0
+    assert L.pasta_set_allocator(None, None, None) == 0
