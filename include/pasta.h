@@ -1,6 +1,7 @@
 /*
- * pasta.h -- C ABI of libpasta: COO MTTKRP and the sparse CP least-squares
- * loss on one NVIDIA GB300 (sm_103a).
+ * pasta.h -- C ABI of libpasta: COO MTTKRP, the sparse CP least-squares
+ * loss and its gradient, CP-ALS, TTV/TTM and TEW-eq/TS on one NVIDIA GB300
+ * (sm_103a).
  *
  * The operations follow arXiv:1902.03317 (PASTA, a sparse tensor benchmark
  * suite):
@@ -17,6 +18,9 @@
  *   - The CP model (a sum of R rank-one terms, Sec. 2.2) fitted by gradient
  *     descent (Sec. 2.2 lists gradient-descent CPD); the loss is the
  *     least-squares objective over the stored entries.
+ *   - CP-ALS, the ALS-based CPD of Sec. 2.2 (steps of the survey it cites).
+ *   - TEW-eq and TS, Sec. 3.1/3.2 and Algorithms 1 and 3; TTV and TTM,
+ *     Sec. 3.3/3.4 and Algorithms 4 and 5.
  *
  * General rules
  *   - Every call returns a pasta_status.  Nothing aborts, throws or traps; a
@@ -50,7 +54,7 @@ extern "C" {
 #define PASTA_MAX_ORDER 8
 #define PASTA_MAX_RANK 256
 #define PASTA_ALS_MAX_RANK 128
-#define PASTA_VERSION 1
+#define PASTA_VERSION 2
 
 typedef struct pasta_coo_s *pasta_coo; /* opaque, owned by the library */
 

@@ -604,8 +604,7 @@ static pasta_status elementwise_output(pasta_coo X, pasta_coo Y, pasta_coo *Z, c
                                        bool *created) {
     *created = false;
     if (!*Z) {
-        pasta_status st = pasta::make_handle(Z, X->order, X->dims, X->nnz,
-                                             const_cast<const uint32_t *const *>(X->orig.idx), nullptr,
+        pasta_status st = pasta::make_handle(Z, X->order, X->dims, X->nnz, X->orig.idx, nullptr,
                                              PASTA_CREATE_NO_VALIDATE, s);
         *created = (st == PASTA_OK);
         return st;

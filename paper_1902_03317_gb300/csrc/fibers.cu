@@ -37,6 +37,10 @@ struct FiberView {
     uint64_t nnz;
 };
 
+struct FiberCoords {
+    uint32_t *idx[kMaxOrder];  // nfibs each, same positions as FiberView
+};
+
 __device__ __forceinline__ bool is_head(const FiberView &v, uint64_t p) {
     if (p == 0) return true;
     bool h = false;
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t *counts, ui
 
 // fid[p] = (heads at or before p) - 1; each head writes its fiber's coordinates.
 __global__ void __launch_bounds__(kThreads) k_fiber_write(FiberView v, const uint32_t *offsets,
-                                                          uint32_t *fid, FiberView out_coords) {
+                                                          uint32_t *fid, FiberCoords out) {
     __shared__ uint32_t wsum[kThreads / 32];
     __shared__ uint32_t running;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -122,8 +126,7 @@ __global__ void __launch_bounds__(kThreads) k_fiber_write(FiberView v, const uin
         if (p < v.nnz) {
             fid[p] = incl - 1u;
             if (h)
-                for (int j = 0; j < v.nm; ++j)
-                    const_cast<uint32_t *>(out_coords.idx[j])[incl - 1u] = v.idx[j][p];
+                for (int j = 0; j < v.nm; ++j) out.idx[j][incl - 1u] = v.idx[j][p];
         }
         __syncthreads();
         if (threadIdx.x == 0)
@@ -267,8 +270,7 @@ pasta_status build_fibers(pasta_coo_s *X, int n, cudaStream_t s) {
         const size_t per = ((size_t)nfibs * 4 + 255) & ~(size_t)255;
         e = dev_malloc(&F.cblock, per * (size_t)(N - 1), s);
         if (e == cudaSuccess) {
-            FiberView out{};
-            out.nm = N - 1;
+            FiberCoords out{};
             for (int j = 0; j < N - 1; ++j) {
                 F.coords[j] = reinterpret_cast<uint32_t *>(static_cast<char *>(F.cblock) + per * j);
                 out.idx[j] = F.coords[j];

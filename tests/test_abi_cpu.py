@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.pasta_version() == 1
+    assert lib.pasta_version() == 2
     for code, name in _lib.STATUS.items():
         assert lib.pasta_status_str(code).decode() == name
 
