@@ -146,14 +146,17 @@ __device__ __forceinline__ void close_run(const Ctx<T, N, KIND> &c,
 
 // One batch: the four entries held at position `src` of the group's chunk.
 // CHECK = false when all four are real entries (every full chunk).
-template <bool CHECK, typename T, int N, int KIND>
+// R0L (loss kinds): 0 = position 0's row, needed where a run starts, is
+// gathered with the others in phase A (a register row per entry); 1 = it is
+// loaded in phase B when the run changes (fewer registers, a dependent load).
+template <bool CHECK, int R0L, typename T, int N, int KIND>
 __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
                                       GroupState<Ctx<T, N, KIND>::VEC> &s, const uint32_t *sb,
                                       int AS, int src, int lim, uint64_t pos) {
     constexpr int VEC = Ctx<T, N, KIND>::VEC;
     constexpr bool MT = (KIND == kMttkrp);
-    constexpr int P0 = MT ? 1 : 0;  // first gathered position
-    constexpr int NR = N - P0;      // rows gathered per entry
+    constexpr int P0 = (MT || R0L) ? 1 : 0;  // first position gathered in phase A
+    constexpr int NR = N - P0;               // rows gathered per entry in phase A
     uint32_t iw[N][4];
     float vw[4];
 #pragma unroll
@@ -201,7 +204,13 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
             }
         }
         if (changed) s.cur = iw[0][q];
-        if (!MT && need0[q]) s.row0 = rows[q][0];
+        if constexpr (!MT && R0L) {
+            if (need0[q])
+                s.row0 = ld_row(reinterpret_cast<const uint4 *>(c.ub[0] + (uint64_t)iw[0][q] * c.stride),
+                                c.pol_rows);
+        } else if (!MT && need0[q]) {
+            s.row0 = rows[q][0];
+        }
         float p[VEC], r[VEC];
         if constexpr (KIND == kMttkrp && NR == 1) {  // order 2: val times one row
             widen<T, VEC>(rows[q][0], r);
@@ -226,10 +235,10 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
             }
         } else {
             // p = prod over positions 1..N-1; model = sum_r p * row0
-            widen<T, VEC>(rows[q][1], p);
+            widen<T, VEC>(rows[q][1 - P0], p);
 #pragma unroll
             for (int k = 2; k < N; ++k) {
-                widen<T, VEC>(rows[q][k], r);
+                widen<T, VEC>(rows[q][k - P0], r);
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) p[e] *= r[e];
             }
@@ -262,7 +271,7 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
 // LC: lanes per entry fixed at compile time (0 = read from Args), which turns
 // every lane-group stride, shared-memory offset and shuffle width into a
 // constant.
-template <typename T, int N, int KIND, int STAGES, int MINB, int LC = 0>
+template <typename T, int N, int KIND, int STAGES, int MINB, int LC = 0, int R0L = 0>
 __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
     constexpr int VEC = 16 / sizeof(T);
     extern __shared__ __align__(16) uint32_t smem[];
@@ -341,10 +350,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
             const uint64_t pos = t0 + (uint64_t)(i * chunk);
             if (__all_sync(kFull, rem >= chunk)) {
                 for (int src = 0; src < L; ++src)
-                    batch<false>(c, s, sb, AS, src, 4, pos + 4u * (uint64_t)src);
+                    batch<false, R0L>(c, s, sb, AS, src, 4, pos + 4u * (uint64_t)src);
             } else {
                 for (int src = 0; src < L; ++src)
-                    batch<true>(c, s, sb, AS, src, rem - 4 * src, pos + 4u * (uint64_t)src);
+                    batch<true, R0L>(c, s, sb, AS, src, rem - 4 * src, pos + 4u * (uint64_t)src);
             }
             if (KIND == kLossFwd || (KIND == kLossBwd && a.partials)) {
                 s.sq += (double)s.sq32;

@@ -21,14 +21,24 @@ constexpr int kStages = 2;
 
 // Blocks per SM each instantiation is compiled for (register budget
 // 65536 / (256 * blocks)), chosen by measurement on the order-3 workloads:
-// occupancy outweighs a few spilled registers for MTTKRP and the forward,
-// not for the backward; higher orders need two blocks' budget.
+// occupancy outweighs a few spilled registers, not many; higher orders need
+// two blocks' budget.
 template <typename T, int N, int KIND>
 constexpr int min_blocks() {
     if (N == 2) return 4;
     if (N != 3) return 2;
-    if (KIND == stream::kLossBwd) return 3;  // the backward spills too much at 4
+    if (KIND == stream::kLossBwd) return sizeof(T) == 4 ? 4 : 3;  // with the late row-0 load
     return sizeof(T) == 4 ? 4 : 3;
+}
+
+// The backward kind loads the sorted mode's row where a run starts, in phase
+// B (R0L = 1), instead of holding a register row per entry of the batch: that
+// let the FP32 order-3 kernel fit 4 blocks per SM with 24 bytes of spills
+// (88 with the row held), 2.24 -> 2.09 ms per zipf3d pass.  It costs uniform
+// cploss3d 5% (0.46 -> 0.48 ms), whose runs and rows sit in L2 anyway.
+template <int KIND>
+constexpr int row0_late() {
+    return KIND == stream::kLossBwd ? 1 : 0;
 }
 
 // LC > 0 compiles the lane count of a row in (LC must equal the geometry's
@@ -53,7 +63,7 @@ pasta_status run(const StreamLaunch &l, cudaStream_t s) {
     a.lshift = g.lshift;
     a.tile = stream::group_tile(g.L);
     const size_t smem = stream::smem_bytes(N, kStages, g.L, l.R);
-    auto kern = k_stream<T, N, KIND, kStages, MINB, LC>;
+    auto kern = k_stream<T, N, KIND, kStages, MINB, LC, row0_late<KIND>()>;
     PASTA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PASTA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
