@@ -130,7 +130,10 @@ pasta_status pasta_coo_info(pasta_coo X, int *order, uint64_t *dims, uint64_t *n
  * taking ceil(log2(dims[k])) bits, truncated to its leading 64 bits; the sort
  * is stable, so entries with equal keys keep creation order.  The copy holds
  * sorted indices, values and the permutation perm (sorted position p holds
- * creation-order entry perm[p]).  A second call for the same mode is a no-op.
+ * creation-order entry perm[p]).  When the key holds every index (the modes'
+ * bits fit 64), the sort carries the values and leaves perm to be built on
+ * first request (pasta_coo_view with d_perm, pasta_coo_copy_out with
+ * d_perm_out), which sorts again.  A second call for the same mode is a no-op.
  * Temporary device memory (about 21 bytes per entry) is the handle's scratch
  * buffer: allocated on first use (cudaMalloc, which waits for the device),
  * reused by later sorts and CP-ALS sweeps on the handle, grown when a call
@@ -143,7 +146,9 @@ pasta_status pasta_coo_sort_by_mode(pasta_coo X, int mode, void *stream);
  * Read-only device views of one stored copy: mode in [0, N) is the
  * mode-sorted copy (PASTA_ERR_NOT_SORTED if absent), mode == -1 the creation
  * order copy (perm is then NULL).  d_idx receives N pointers.  The pointers
- * stay valid until pasta_coo_destroy.  Any output pointer may be NULL.
+ * stay valid until pasta_coo_destroy.  Any output pointer may be NULL.  Asking
+ * for d_perm of a copy whose permutation was left out builds it on the
+ * legacy default stream and waits for it.
  */
 pasta_status pasta_coo_view(pasta_coo X, int mode, const uint32_t **d_idx,
                             const float **d_val, const uint32_t **d_perm);

@@ -414,6 +414,12 @@ pasta_status pasta_coo_view(pasta_coo X, int mode, const uint32_t **d_idx, const
     if (d_idx)
         for (int k = 0; k < X->order; ++k) d_idx[k] = c.idx[k];
     if (d_val) *d_val = c.val;
+    if (d_perm && mode >= 0 && !c.perm_ready) {
+        // built on first request, on the legacy default stream, and waited for
+        pasta_status st = ensure_perm(X, mode, nullptr);
+        if (st != PASTA_OK) return st;
+        PASTA_CUDA(cudaStreamSynchronize(nullptr));
+    }
     if (d_perm) *d_perm = c.perm;
     return PASTA_OK;
 }
@@ -437,7 +443,11 @@ pasta_status pasta_coo_copy_out(pasta_coo X, int mode, uint32_t *const *d_idx_ou
             if (d_idx_out[k])
                 PASTA_CUDA(cudaMemcpyAsync(d_idx_out[k], c.idx[k], bytes, cudaMemcpyDeviceToDevice, s));
     if (d_val_out) PASTA_CUDA(cudaMemcpyAsync(d_val_out, c.val, bytes, cudaMemcpyDeviceToDevice, s));
-    if (d_perm_out) PASTA_CUDA(cudaMemcpyAsync(d_perm_out, c.perm, bytes, cudaMemcpyDeviceToDevice, s));
+    if (d_perm_out) {
+        pasta_status st = ensure_perm(X, mode, s);
+        if (st != PASTA_OK) return st;
+        PASTA_CUDA(cudaMemcpyAsync(d_perm_out, c.perm, bytes, cudaMemcpyDeviceToDevice, s));
+    }
     return PASTA_OK;
 }
 

@@ -40,6 +40,7 @@ struct StoredCopy {
     uint32_t *idx[kMaxOrder] = {};
     float *val = nullptr;
     uint32_t *perm = nullptr;  // sorted position -> creation-order entry (sorted copies)
+    bool perm_ready = false;   // perm computed (built on request when the sort did not need it)
     void *block = nullptr;     // the allocation holding all arrays
     bool present = false;
 };
@@ -122,6 +123,8 @@ pasta_status validate_coo(const pasta_coo_s *X, void *stream, uint64_t *bad_inde
                           uint64_t *bad_value);
 
 pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t stream);
+// Computes the mode's sorted-copy permutation if the sort left it out.
+pasta_status ensure_perm(pasta_coo_s *X, int mode, cudaStream_t stream);
 
 pasta_status launch_mttkrp(const pasta_coo_s *X, const StoredCopy &c, const void *const *U,
                            pasta_dtype dt, int mode, int R, void *M, cudaStream_t stream);

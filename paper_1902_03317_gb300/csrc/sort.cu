@@ -5,10 +5,14 @@
 // The key of entry m is its coordinate in cyclic mode order starting at the
 // sorted mode, each mode taking ceil(log2(dims[k])) bits, cut to the leading
 // 64 bits.  A stable least-significant-digit radix sort (8-bit digits) of
-// (key, entry number) pairs gives the permutation; a final pass writes the
-// sorted SoA copy, decoding every index the key holds whole from the sorted
-// keys and gathering only the rest (and the values) through the permutation.
-// Equal keys keep creation order, so the result is unique.
+// (key, payload) pairs orders the entries; equal keys keep creation order, so
+// the result is unique.  When the key holds every index whole (the common
+// case: the modes' bits fit 64), the payload is the value itself and the
+// indices are decoded from the sorted keys, so nothing is gathered; the
+// permutation (sorted position -> creation-order entry), which no kernel
+// needs, is sorted for only when a caller asks for it.  Otherwise the
+// payload is the entry number and a final pass gathers the indices the key
+// does not hold, and the values, through the resulting permutation.
 //
 // Radix pass = histogram per 4096-entry tile (digit-major table), exclusive
 // scan of each digit's row over tiles, stable scatter: each warp ranks its
@@ -35,7 +39,9 @@ struct KeySpec {
     int final_shift;      // key >>= final_shift (right-aligns the used bits)
 };
 
-__global__ void k_make_keys(CooView v, KeySpec ks, uint64_t *keys, uint32_t *perm) {
+// keys[m] = the key of entry m; payload[m] = its value's bits (payload_val)
+// or its creation-order number.
+__global__ void k_make_keys(CooView v, KeySpec ks, uint64_t *keys, uint32_t *payload, bool payload_val) {
     for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.nnz;
          m += (uint64_t)gridDim.x * blockDim.x) {
         uint64_t key = 0;
@@ -47,7 +53,7 @@ __global__ void k_make_keys(CooView v, KeySpec ks, uint64_t *keys, uint32_t *per
             }
         }
         keys[m] = ks.final_shift >= 64 ? 0 : (key >> ks.final_shift);
-        perm[m] = (uint32_t)m;
+        payload[m] = payload_val ? __float_as_uint(v.val[m]) : (uint32_t)m;
     }
 }
 
@@ -314,19 +320,27 @@ __global__ void __launch_bounds__(256) k_gather(CooView src, const uint32_t *per
     }
 }
 
+// Writes the sorted copy's indices when the key holds every one of them
+// (the values arrived as the sort's payload).
+__global__ void k_decode(const uint64_t *keys, uint64_t n, int order, GatherDst dst) {
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t key = keys[p];
+#pragma unroll
+        for (int k = 0; k < kMaxOrder; ++k)
+            if (k < order) dst.idx[k][p] = (uint32_t)(key >> dst.shift[k]) & dst.mask[k];
+    }
+}
+
 int bits_for(uint64_t dim) {
     int b = 0;
     while (b < 64 && (dim - 1) >> b) ++b;
     return b;
 }
 
-}  // namespace
-
-pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
-    StoredCopy &dst = X->sorted[mode];
-    const uint64_t n = X->nnz;
-    if (n == 0) return PASTA_OK;
-
+// Key layout of a mode-n copy: cyclic mode order from n, each mode
+// ceil(log2 dims) bits, cut to the leading 64 bits.  *used = bits kept.
+KeySpec key_spec(const pasta_coo_s *X, int mode, int *used_out) {
     KeySpec ks{};
     ks.order = X->order;
     int used = 0;
@@ -347,38 +361,12 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
         }
     }
     ks.final_shift = 64 - used;
-    const int passes = (used + 7) / 8;
+    *used_out = used;
+    return ks;
+}
 
-    const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
-    // scratch: two key buffers, the spare permutation buffer, the histograms
-    const size_t hist_n = (size_t)256 * ntiles + 256;
-    const size_t keys_b = (2 * n * sizeof(uint64_t) + 255) & ~(size_t)255;
-    const size_t tmpv_b = (n * sizeof(uint32_t) + 255) & ~(size_t)255;
-    void *base = nullptr;
-    pasta_status sst = handle_scratch(X, keys_b + tmpv_b + hist_n * sizeof(uint32_t), &base);
-    if (sst != PASTA_OK) return sst;
-    uint64_t *keys = reinterpret_cast<uint64_t *>(base);
-    uint32_t *tmpv = reinterpret_cast<uint32_t *>(static_cast<char *>(base) + keys_b);
-    uint32_t *hist = reinterpret_cast<uint32_t *>(static_cast<char *>(base) + keys_b + tmpv_b);
-    uint64_t *kb[2] = {keys, keys + n};
-    uint32_t *vb[2];
-    vb[passes % 2] = dst.perm;  // the last pass writes into the copy's perm
-    vb[1 - passes % 2] = tmpv;
-    uint32_t *totals = hist + (size_t)256 * ntiles;
-
-    PASTA_CUDA(cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)kScatterSmem));
-    const CooView src = view_of(X, X->orig);
-    const int gblocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16);
-    pasta_status st = PASTA_OK;
-    k_make_keys<<<gblocks, 256, 0, s>>>(src, ks, kb[0], vb[0]);
-    for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        k_hist<<<ntiles, kThreads, 0, s>>>(kb[p % 2], n, shift, ntiles, hist);
-        k_rowscan<<<256, 1024, 0, s>>>(hist, ntiles, totals);
-        k_scatter<<<ntiles, kThreads, kScatterSmem, s>>>(kb[p % 2], vb[p % 2], kb[(p + 1) % 2],
-                                              vb[(p + 1) % 2], n, shift, ntiles, hist, totals);
-    }
+// Where each mode's index sits in the sorted key (shift < 0: not whole).
+GatherDst decode_spec(const pasta_coo_s *X, const KeySpec &ks, const StoredCopy &dst) {
     GatherDst gd{};
     for (int k = 0; k < X->order; ++k) {
         gd.idx[k] = dst.idx[k];
@@ -396,9 +384,99 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
         }
     }
     gd.val = dst.val;
-    k_gather<<<gblocks, 256, 0, s>>>(src, dst.perm, kb[passes % 2], gd);
+    return gd;
+}
+
+// Stable LSD radix sort of (key, payload) pairs made from the creation-order
+// copy: payload = the value bits (payload_val) or the entry number.  The
+// sorted payload lands in payload_out (nnz words); *keys_sorted points at the
+// sorted keys inside the handle's scratch (valid until its next use).
+pasta_status radix_sort(pasta_coo_s *X, const KeySpec &ks, int used, bool payload_val,
+                        uint32_t *payload_out, const uint64_t **keys_sorted, cudaStream_t s) {
+    const uint64_t n = X->nnz;
+    const int passes = (used + 7) / 8;
+    const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
+    // scratch: two key buffers, the spare payload buffer, the histograms
+    const size_t hist_n = (size_t)256 * ntiles + 256;
+    const size_t keys_b = (2 * n * sizeof(uint64_t) + 255) & ~(size_t)255;
+    const size_t tmpv_b = (n * sizeof(uint32_t) + 255) & ~(size_t)255;
+    void *base = nullptr;
+    pasta_status st = handle_scratch(X, keys_b + tmpv_b + hist_n * sizeof(uint32_t), &base);
+    if (st != PASTA_OK) return st;
+    uint64_t *keys = reinterpret_cast<uint64_t *>(base);
+    uint32_t *tmpv = reinterpret_cast<uint32_t *>(static_cast<char *>(base) + keys_b);
+    uint32_t *hist = reinterpret_cast<uint32_t *>(static_cast<char *>(base) + keys_b + tmpv_b);
+    uint64_t *kb[2] = {keys, keys + n};
+    uint32_t *vb[2];
+    vb[passes % 2] = payload_out;  // the last pass writes into payload_out
+    vb[1 - passes % 2] = tmpv;
+    uint32_t *totals = hist + (size_t)256 * ntiles;
+
+    PASTA_CUDA(cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kScatterSmem));
+    const CooView src = view_of(X, X->orig);
+    const int gblocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16);
+    k_make_keys<<<gblocks, 256, 0, s>>>(src, ks, kb[0], vb[0], payload_val);
+    for (int p = 0; p < passes; ++p) {
+        const int shift = 8 * p;
+        k_hist<<<ntiles, kThreads, 0, s>>>(kb[p % 2], n, shift, ntiles, hist);
+        k_rowscan<<<256, 1024, 0, s>>>(hist, ntiles, totals);
+        k_scatter<<<ntiles, kThreads, kScatterSmem, s>>>(kb[p % 2], vb[p % 2], kb[(p + 1) % 2],
+                                                         vb[(p + 1) % 2], n, shift, ntiles, hist, totals);
+    }
+    PASTA_CUDA(cudaGetLastError());
+    *keys_sorted = kb[passes % 2];
+    return PASTA_OK;
+}
+
+bool key_holds_all(const GatherDst &gd, int order) {
+    for (int k = 0; k < order; ++k)
+        if (gd.shift[k] < 0) return false;
+    return true;
+}
+
+}  // namespace
+
+pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
+    StoredCopy &dst = X->sorted[mode];
+    const uint64_t n = X->nnz;
+    dst.perm_ready = false;
+    if (n == 0) {
+        dst.perm_ready = true;
+        return PASTA_OK;
+    }
+    int used = 0;
+    const KeySpec ks = key_spec(X, mode, &used);
+    const GatherDst gd = decode_spec(X, ks, dst);
+    const int gblocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16);
+    const uint64_t *keys = nullptr;
+    if (key_holds_all(gd, X->order)) {
+        // the values travel as the payload and every index is decoded from
+        // the sorted keys: nothing is gathered; the permutation is built on
+        // request (ensure_perm)
+        pasta_status st = radix_sort(X, ks, used, true, reinterpret_cast<uint32_t *>(dst.val), &keys, s);
+        if (st != PASTA_OK) return st;
+        k_decode<<<gblocks, 256, 0, s>>>(keys, n, X->order, gd);
+    } else {
+        pasta_status st = radix_sort(X, ks, used, false, dst.perm, &keys, s);
+        if (st != PASTA_OK) return st;
+        const CooView src = view_of(X, X->orig);
+        k_gather<<<gblocks, 256, 0, s>>>(src, dst.perm, keys, gd);
+        dst.perm_ready = true;
+    }
     cudaError_t le = cudaGetLastError();
-    if (le != cudaSuccess) st = cuda_fail(le, "sort kernels");
+    if (le != cudaSuccess) return cuda_fail(le, "sort kernels");
+    return PASTA_OK;
+}
+
+pasta_status ensure_perm(pasta_coo_s *X, int mode, cudaStream_t s) {
+    StoredCopy &c = X->sorted[mode];
+    if (!c.present || c.perm_ready) return PASTA_OK;
+    int used = 0;
+    const KeySpec ks = key_spec(X, mode, &used);
+    const uint64_t *keys = nullptr;
+    pasta_status st = radix_sort(X, ks, used, false, c.perm, &keys, s);
+    if (st == PASTA_OK) c.perm_ready = true;
     return st;
 }
 
