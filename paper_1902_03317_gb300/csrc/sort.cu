@@ -4,7 +4,7 @@
 //
 // The key of entry m is its coordinate in cyclic mode order starting at the
 // sorted mode, each mode taking ceil(log2(dims[k])) bits, cut to the leading
-// 64 bits.  A stable least-significant-digit radix sort (8-bit digits) of
+// 64 bits.  A stable least-significant-digit radix sort (digits of up to 9 bits) of
 // (key, payload) pairs orders the entries; equal keys keep creation order, so
 // the result is unique.  When the key holds every index whole (the common
 // case: the modes' bits fit 64), the payload is the value itself and the
@@ -14,6 +14,7 @@
 // payload is the entry number and a final pass gathers the indices the key
 // does not hold, and the values, through the resulting permutation.
 //
+// Digits have up to 9 bits, balanced over the fewest passes.
 // Radix pass = histogram per 4096-entry tile (digit-major table), exclusive
 // scan of each digit's row over tiles, stable scatter: each warp ranks its
 // 512-entry sub-tile by digit in storage order, the tile is reordered by
@@ -64,26 +65,21 @@ __global__ void k_make_keys(CooView v, KeySpec ks, uint64_t *keys, uint32_t *pay
 constexpr int kWarpsPerBlock = kThreads / 32;
 constexpr int kItems = kTile / kThreads;
 constexpr int kWarpSpan = 32 * kItems;
-constexpr int kBins = 256;
+constexpr int kMaxBins = 512;  // digits of up to 9 bits
 static_assert(kWarpSpan <= 65536, "warp ranks are packed as 16-bit values");
 
-// Digit of a key for the pass at `shift`; entries past the end get a value
-// unique to their lane (>= kBins), so they match no real digit.
-__device__ __forceinline__ uint32_t digit_of(uint64_t key, int shift) {
-    return (uint32_t)(key >> shift) & (kBins - 1);
-}
-
-// hist[d * ntiles + tile] = number of entries of `tile` whose digit is d.
-// Plain shared atomics per entry (one sub-histogram per warp); measured
-// faster than aggregating equal digits with __match_any_sync first.
+// hist[d * ntiles + tile] = number of entries of `tile` whose digit
+// ((key >> shift) & mask, below BINS) is d.  Plain shared atomics per entry
+// (one sub-histogram per warp); measured faster than aggregating equal digits
+// with __match_any_sync first.
+template <int BINS>
 __global__ void __launch_bounds__(kThreads) k_hist(const uint64_t *keys, uint64_t n, int shift,
-                                                   uint32_t ntiles, uint32_t *hist) {
-    __shared__ uint32_t cnt[kWarpsPerBlock][kBins];
+                                                   uint32_t mask, uint32_t ntiles, uint32_t *hist) {
+    __shared__ uint32_t cnt[kWarpsPerBlock][BINS];
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
-#pragma unroll
-    for (int w = 0; w < kWarpsPerBlock; ++w) cnt[w][t] = 0;
+    for (int i = t; i < kWarpsPerBlock * BINS; i += kThreads) (&cnt[0][0])[i] = 0;
     __syncthreads();
     const uint64_t base = (uint64_t)blockIdx.x * kTile + (uint64_t)warp * kWarpSpan + lane;
     const int64_t rem = (int64_t)n - (int64_t)base;  // entry j is real iff 32 j < rem
@@ -93,15 +89,16 @@ __global__ void __launch_bounds__(kThreads) k_hist(const uint64_t *keys, uint64_
     for (int j = 0; j < kItems; ++j) k[j] = 32 * j < rem ? kp[32 * j] : 0ull;
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
-        const bool valid = 32 * j < rem;
-        const uint32_t d = digit_of(k[j], shift);
-        if (valid) atomicAdd(&cnt[warp][d], 1u);
+        const uint32_t d = (uint32_t)(k[j] >> shift) & mask;
+        if (32 * j < rem) atomicAdd(&cnt[warp][d], 1u);
     }
     __syncthreads();
-    uint32_t c = 0;
+    for (int d = t; d < BINS; d += kThreads) {
+        uint32_t c = 0;
 #pragma unroll
-    for (int w = 0; w < kWarpsPerBlock; ++w) c += cnt[w][t];
-    hist[(uint64_t)t * ntiles + blockIdx.x] = c;
+        for (int w = 0; w < kWarpsPerBlock; ++w) c += cnt[w][d];
+        hist[(uint64_t)d * ntiles + blockIdx.x] = c;
+    }
 }
 
 // Exclusive scan of row d (one block per digit) of the digit-major table;
@@ -146,6 +143,23 @@ __global__ void __launch_bounds__(1024) k_rowscan(uint32_t *hist, uint32_t ntile
 // Shared memory of k_scatter: the tile's keys and values in digit order.
 constexpr size_t kScatterSmem = (size_t)kTile * (sizeof(uint64_t) + sizeof(uint32_t));
 
+// Exclusive scan over the block of one value per thread (thread order);
+// every thread must call it.  wsum: kWarpsPerBlock words of shared memory.
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t x, uint32_t *wsum) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();  // wsum may still be read from a previous call
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    uint32_t before = 0;
+    for (int w = 0; w < warp; ++w) before += wsum[w];
+    return before + inc - x;
+}
+
 // Stable scatter of one tile.  (1) Each warp ranks its sub-tile round by
 // round: __match_any_sync finds the lanes of equal digit (measured faster
 // here than a shared-memory mask word per digit), the lowest of them reads
@@ -154,24 +168,27 @@ constexpr size_t kScatterSmem = (size_t)kTile * (sizeof(uint64_t) + sizeof(uint3
 // digit, warp offsets and the tile-local start follow from those counts.
 // (3) The tile is reordered by digit in shared memory, and (4) written out in
 // that order: consecutive threads write consecutive positions of one digit's
-// output range, so the writes coalesce.
+// output range, so the writes coalesce.  Thread t owns digits t * PER ...
+// t * PER + PER - 1 in the per-digit steps.
+template <int BINS>
 __global__ void __launch_bounds__(kThreads, 2)
     k_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout,
-              uint64_t n, int shift, uint32_t ntiles, const uint32_t *hist,
+              uint64_t n, int shift, uint32_t mask, uint32_t ntiles, const uint32_t *hist,
               const uint32_t *totals) {
+    constexpr int PER = BINS / kThreads;
+    static_assert(PER >= 1 && PER * kThreads == BINS, "BINS must be a multiple of the block");
     extern __shared__ __align__(16) unsigned char sm_raw[];
     uint64_t *sk = reinterpret_cast<uint64_t *>(sm_raw);
     uint32_t *sv = reinterpret_cast<uint32_t *>(sm_raw + (size_t)kTile * sizeof(uint64_t));
-    __shared__ uint32_t wcnt[kWarpsPerBlock][kBins];  // per-warp counts, then warp offsets
-    __shared__ uint32_t lstart[kBins];                // tile-local start of each digit
-    __shared__ uint32_t gbase[kBins];                 // output position of that start
+    __shared__ uint32_t wcnt[kWarpsPerBlock][BINS];  // per-warp counts, then warp offsets
+    __shared__ uint32_t lstart[BINS];                // tile-local start of each digit
+    __shared__ uint32_t gbase[BINS];                 // output position of that start
     __shared__ uint32_t wsum[kWarpsPerBlock];
     const int t = threadIdx.x;
     const int lane = t & 31;
     const int warp = t >> 5;
     const unsigned lt = (1u << lane) - 1u;
-#pragma unroll
-    for (int w = 0; w < kWarpsPerBlock; ++w) wcnt[w][t] = 0;
+    for (int i = t; i < kWarpsPerBlock * BINS; i += kThreads) (&wcnt[0][0])[i] = 0;
 
     const uint64_t tbase = (uint64_t)blockIdx.x * kTile;
     const int tlen = (int)min((uint64_t)kTile, n - tbase);
@@ -183,27 +200,29 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll
     for (int j = 0; j < kItems; ++j) k[j] = 32 * j < rem ? kp[32 * j] : 0ull;
     // Exclusive scan of the digit totals (digit base of this pass) plus this
-    // tile's scanned count: where the tile's first entry of digit t goes.
+    // tile's scanned count: where the tile's first entry of each digit goes.
     {
-        const uint32_t x = totals[t];
-        uint32_t inc = x;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, inc, o);
-            if (lane >= o) inc += y;
+        uint32_t x[PER], sum = 0;
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            x[u] = totals[t * PER + u];
+            sum += x[u];
         }
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();  // also orders the wcnt zeroing before the ranking
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += wsum[w];
-        gbase[t] = before + inc - x + hist[(uint64_t)t * ntiles + blockIdx.x];
+        uint32_t ex = block_exclusive(sum, wsum);  // its barriers also order the zeroing above
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            const int d = t * PER + u;
+            gbase[d] = ex + hist[(uint64_t)d * ntiles + blockIdx.x];
+            ex += x[u];
+        }
     }
     // (1) warp ranks (< kWarpSpan, two per register)
     uint32_t r[kItems / 2];
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         const bool valid = 32 * j < rem;
-        const uint32_t d = digit_of(k[j], shift);
-        const unsigned peers = __match_any_sync(FULL, valid ? d : kBins + lane);
+        const uint32_t d = (uint32_t)(k[j] >> shift) & mask;
+        const unsigned peers = __match_any_sync(FULL, valid ? d : BINS + lane);
         const int leader = __ffs(peers) - 1;
         uint32_t old = 0;
         if (valid && lane == leader) {
@@ -224,31 +243,33 @@ __global__ void __launch_bounds__(kThreads, 2)
     __syncthreads();
     // (2) warp offsets per digit, then the tile-local digit starts
     {
-        uint32_t run = 0;
+        uint32_t tot[PER], sum = 0;
 #pragma unroll
-        for (int w = 0; w < kWarpsPerBlock; ++w) {
-            const uint32_t c = wcnt[w][t];
-            wcnt[w][t] = run;
-            run += c;
+        for (int u = 0; u < PER; ++u) {
+            const int d = t * PER + u;
+            uint32_t run = 0;
+#pragma unroll
+            for (int w = 0; w < kWarpsPerBlock; ++w) {
+                const uint32_t c = wcnt[w][d];
+                wcnt[w][d] = run;
+                run += c;
+            }
+            tot[u] = run;
+            sum += run;
         }
-        uint32_t inc = run;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(FULL, inc, o);
-            if (lane >= o) inc += y;
+        uint32_t ex = block_exclusive(sum, wsum);
+#pragma unroll
+        for (int u = 0; u < PER; ++u) {
+            lstart[t * PER + u] = ex;
+            ex += tot[u];
         }
-        __syncthreads();  // wsum is reused
-        if (lane == 31) wsum[warp] = inc;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += wsum[w];
-        lstart[t] = before + inc - run;
     }
     __syncthreads();
     // (3) reorder the tile by digit in shared memory
 #pragma unroll
     for (int j = 0; j < kItems; ++j) {
         if (32 * j < rem) {
-            const uint32_t d = digit_of(k[j], shift);
+            const uint32_t d = (uint32_t)(k[j] >> shift) & mask;
             const uint32_t lp = lstart[d] + wcnt[warp][d] + ((r[j / 2] >> (16 * (j & 1))) & 0xFFFFu);
             sk[lp] = k[j];
             sv[lp] = v[j];
@@ -259,7 +280,7 @@ __global__ void __launch_bounds__(kThreads, 2)
 #pragma unroll 4
     for (int q = t; q < tlen; q += kThreads) {
         const uint64_t key = sk[q];
-        const uint32_t d = digit_of(key, shift);
+        const uint32_t d = (uint32_t)(key >> shift) & mask;
         const uint64_t gp = (uint64_t)gbase[d] + (uint32_t)(q - (int)lstart[d]);
         kout[gp] = key;
         vout[gp] = sv[q];
@@ -394,10 +415,12 @@ GatherDst decode_spec(const pasta_coo_s *X, const KeySpec &ks, const StoredCopy 
 pasta_status radix_sort(pasta_coo_s *X, const KeySpec &ks, int used, bool payload_val,
                         uint32_t *payload_out, const uint64_t **keys_sorted, cudaStream_t s) {
     const uint64_t n = X->nnz;
-    const int passes = (used + 7) / 8;
+    // digits of at most 9 bits, balanced over the fewest passes: 57 bits take
+    // 7 passes (one of 9 bits), 64 take 8 of 8
+    const int passes = (used + 8) / 9;
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
     // scratch: two key buffers, the spare payload buffer, the histograms
-    const size_t hist_n = (size_t)256 * ntiles + 256;
+    const size_t hist_n = (size_t)kMaxBins * ntiles + kMaxBins;
     const size_t keys_b = (2 * n * sizeof(uint64_t) + 255) & ~(size_t)255;
     const size_t tmpv_b = (n * sizeof(uint32_t) + 255) & ~(size_t)255;
     void *base = nullptr;
@@ -410,19 +433,33 @@ pasta_status radix_sort(pasta_coo_s *X, const KeySpec &ks, int used, bool payloa
     uint32_t *vb[2];
     vb[passes % 2] = payload_out;  // the last pass writes into payload_out
     vb[1 - passes % 2] = tmpv;
-    uint32_t *totals = hist + (size_t)256 * ntiles;
+    uint32_t *totals = hist + (size_t)kMaxBins * ntiles;
 
-    PASTA_CUDA(cudaFuncSetAttribute(k_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    PASTA_CUDA(cudaFuncSetAttribute(k_scatter<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kScatterSmem));
+    PASTA_CUDA(cudaFuncSetAttribute(k_scatter<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kScatterSmem));
     const CooView src = view_of(X, X->orig);
     const int gblocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16);
     k_make_keys<<<gblocks, 256, 0, s>>>(src, ks, kb[0], vb[0], payload_val);
+    int shift = 0;
     for (int p = 0; p < passes; ++p) {
-        const int shift = 8 * p;
-        k_hist<<<ntiles, kThreads, 0, s>>>(kb[p % 2], n, shift, ntiles, hist);
-        k_rowscan<<<256, 1024, 0, s>>>(hist, ntiles, totals);
-        k_scatter<<<ntiles, kThreads, kScatterSmem, s>>>(kb[p % 2], vb[p % 2], kb[(p + 1) % 2],
-                                                         vb[(p + 1) % 2], n, shift, ntiles, hist, totals);
+        const int width = used / passes + (p < used % passes ? 1 : 0);  // 1..9 bits
+        const uint32_t mask = (1u << width) - 1u;
+        const uint64_t *ki = kb[p % 2];
+        uint64_t *ko = kb[(p + 1) % 2];
+        if (width > 8) {
+            k_hist<512><<<ntiles, kThreads, 0, s>>>(ki, n, shift, mask, ntiles, hist);
+            k_rowscan<<<512, 1024, 0, s>>>(hist, ntiles, totals);
+            k_scatter<512><<<ntiles, kThreads, kScatterSmem, s>>>(ki, vb[p % 2], ko, vb[(p + 1) % 2], n,
+                                                                  shift, mask, ntiles, hist, totals);
+        } else {
+            k_hist<256><<<ntiles, kThreads, 0, s>>>(ki, n, shift, mask, ntiles, hist);
+            k_rowscan<<<256, 1024, 0, s>>>(hist, ntiles, totals);
+            k_scatter<256><<<ntiles, kThreads, kScatterSmem, s>>>(ki, vb[p % 2], ko, vb[(p + 1) % 2], n,
+                                                                  shift, mask, ntiles, hist, totals);
+        }
+        shift += width;
     }
     PASTA_CUDA(cudaGetLastError());
     *keys_sorted = kb[passes % 2];
