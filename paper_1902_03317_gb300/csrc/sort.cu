@@ -408,16 +408,20 @@ GatherDst decode_spec(const pasta_coo_s *X, const KeySpec &ks, const StoredCopy 
     return gd;
 }
 
-// Stable LSD radix sort of (key, payload) pairs made from the creation-order
-// copy: payload = the value bits (payload_val) or the entry number.  The
+// Stable LSD radix sort of (key, payload) pairs made from the stored copy
+// srcc: payload = the value bits (payload_val) or the entry number (then srcc
+// must be the creation-order copy).  The passes cover key bits [low, used):
+// low > 0 when srcc is already ordered by the low bits (see sort_copy).  The
 // sorted payload lands in payload_out (nnz words); *keys_sorted points at the
 // sorted keys inside the handle's scratch (valid until its next use).
-pasta_status radix_sort(pasta_coo_s *X, const KeySpec &ks, int used, bool payload_val,
-                        uint32_t *payload_out, const uint64_t **keys_sorted, cudaStream_t s) {
+pasta_status radix_sort(pasta_coo_s *X, const StoredCopy &srcc, const KeySpec &ks, int low, int used,
+                        bool payload_val, uint32_t *payload_out, const uint64_t **keys_sorted,
+                        cudaStream_t s) {
     const uint64_t n = X->nnz;
     // digits of at most 9 bits, balanced over the fewest passes: 57 bits take
     // 7 passes (one of 9 bits), 64 take 8 of 8
-    const int passes = (used + 8) / 9;
+    const int bits = used - low;
+    const int passes = (bits + 8) / 9;
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
     // scratch: two key buffers, the spare payload buffer, the histograms
     const size_t hist_n = (size_t)kMaxBins * ntiles + kMaxBins;
@@ -439,12 +443,12 @@ pasta_status radix_sort(pasta_coo_s *X, const KeySpec &ks, int used, bool payloa
                                     (int)kScatterSmem));
     PASTA_CUDA(cudaFuncSetAttribute(k_scatter<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kScatterSmem));
-    const CooView src = view_of(X, X->orig);
+    const CooView src = view_of(X, srcc);
     const int gblocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16);
     k_make_keys<<<gblocks, 256, 0, s>>>(src, ks, kb[0], vb[0], payload_val);
-    int shift = 0;
+    int shift = low;
     for (int p = 0; p < passes; ++p) {
-        const int width = used / passes + (p < used % passes ? 1 : 0);  // 1..9 bits
+        const int width = bits / passes + (p < bits % passes ? 1 : 0);  // 1..9 bits
         const uint32_t mask = (1u << width) - 1u;
         const uint64_t *ki = kb[p % 2];
         uint64_t *ko = kb[(p + 1) % 2];
@@ -490,12 +494,21 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
     if (key_holds_all(gd, X->order)) {
         // the values travel as the payload and every index is decoded from
         // the sorted keys: nothing is gathered; the permutation is built on
-        // request (ensure_perm)
-        pasta_status st = radix_sort(X, ks, used, true, reinterpret_cast<uint32_t *>(dst.val), &keys, s);
+        // request (ensure_perm).  The key's least significant field is mode
+        // n-1; if the mode-(n-1) sorted copy exists it is already ordered by
+        // that field (it leads its own key), so a stable sort of it on the
+        // other fields alone gives the same order (ties in them keep the
+        // copy's order: by mode n-1, then creation order).
+        const int prev = (mode + X->order - 1) % X->order;
+        const StoredCopy &pc = X->sorted[prev];
+        const bool derive = prev != mode && pc.present;
+        const int low = derive ? bits_for(X->dims[prev]) : 0;
+        pasta_status st = radix_sort(X, derive ? pc : X->orig, ks, low, used, true,
+                                     reinterpret_cast<uint32_t *>(dst.val), &keys, s);
         if (st != PASTA_OK) return st;
         k_decode<<<gblocks, 256, 0, s>>>(keys, n, X->order, gd);
     } else {
-        pasta_status st = radix_sort(X, ks, used, false, dst.perm, &keys, s);
+        pasta_status st = radix_sort(X, X->orig, ks, 0, used, false, dst.perm, &keys, s);
         if (st != PASTA_OK) return st;
         const CooView src = view_of(X, X->orig);
         k_gather<<<gblocks, 256, 0, s>>>(src, dst.perm, keys, gd);
@@ -512,7 +525,7 @@ pasta_status ensure_perm(pasta_coo_s *X, int mode, cudaStream_t s) {
     int used = 0;
     const KeySpec ks = key_spec(X, mode, &used);
     const uint64_t *keys = nullptr;
-    pasta_status st = radix_sort(X, ks, used, false, c.perm, &keys, s);
+    pasta_status st = radix_sort(X, X->orig, ks, 0, used, false, c.perm, &keys, s);
     if (st == PASTA_OK) c.perm_ready = true;
     return st;
 }

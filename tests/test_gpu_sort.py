@@ -42,6 +42,28 @@ def test_sorted_copies_match_oracle_exactly(name, nnz, dims):
     X.close()
 
 
+@pytest.mark.parametrize("name,nnz,dims", CASES[:3])
+def test_sort_order_independent_of_which_copies_exist(name, nnz, dims):
+    """A mode's copy may be sorted from the previous mode's copy (already
+    ordered by the key's last field); the result must equal the sort from
+    the creation order whatever was sorted before."""
+    Xh = G.synth.generate(G.small(name, nnz, dims))
+    idx, val = G.host(Xh)
+    N = len(dims)
+    for sequence in (list(reversed(range(N))), [1, 0] + list(range(2, N))):
+        X = G.to_device(Xh)
+        for mode in sequence:
+            X.sort_by_mode(mode)
+        for mode in range(N):
+            sidx, sval, perm = X.copy_out(mode)
+            perm = perm.cpu().numpy().astype(np.int64)
+            np.testing.assert_array_equal(perm, oracle.sort_perm(idx, mode))
+            for k in range(N):
+                np.testing.assert_array_equal(sidx[k].cpu().numpy().astype(np.uint32), idx[k][perm])
+            np.testing.assert_array_equal(sval.cpu().numpy(), val[perm].astype(np.float32))
+        X.close()
+
+
 def test_key_cut_to_64_bits_keeps_leading_modes_sorted():
     # 3 + 24 + 21 + 17 + 10 = 75 bits: the key holds modes 0,1,2 and the top
     # 16 bits of mode 3 when sorting for mode 0.
