@@ -539,11 +539,14 @@ def e2e(pasta, synth, wl, dev, args, world):
     X.close()
     del Ms, Us
     mark("destroy", t)
-    steps = max(2, min(args.steps, 3))
+    steps = max(2, min(args.steps, 5))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    per_step = []
     for _ in range(steps):
+        ts = time.perf_counter()
         one()
+        per_step.append(round((time.perf_counter() - ts) * 1e3, 2))
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
     if world > 1:
@@ -555,7 +558,7 @@ def e2e(pasta, synth, wl, dev, args, world):
     return {"value": world * N * wl.nnz / dt, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": steps,
             "includes": "H2D of COO+factors, create, sort every mode, MTTKRP every mode, D2H of outputs",
-            "breakdown_ms": br}
+            "breakdown_ms": br, "per_step_ms": per_step}
 
 
 # ----------------------------------------------------------- CPU oracle --
