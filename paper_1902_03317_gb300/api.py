@@ -1,11 +1,15 @@
-"""Python API over libpasta: COO handles, MTTKRP, CP loss and its autograd.
+"""Python API over libpasta: COO handles, MTTKRP, the CP loss and its
+autograd, CP-ALS, TEW-eq/TS and TTV/TTM.
 
-PyTorch supplies device memory and the current CUDA stream; every step of the
+PyTorch supplies device memory (its caching allocator also backs the
+library's own buffers) and the current CUDA stream; every step of the
 computation (copy-in and validation, mode sort, MTTKRP, loss forward and
-backward, gradient down-conversion) runs in libpasta's kernels.  Operations
-follow arXiv:1902.03317 (PASTA): COO storage (Sec. 5.1), mode-order sorting
-(Sec. 5.2.2), MTTKRP (Eq. (mttkrp-init), Algorithm 6) and the CP model behind
-gradient-descent CPD (Sec. 2.2).
+backward, gradient down-conversion, the ALS solve, the element-wise and
+mode-n products) runs in libpasta's kernels.  Operations follow
+arXiv:1902.03317 (PASTA): COO storage (Sec. 5.1), mode-order sorting
+(Sec. 5.2.2), MTTKRP (Eq. (mttkrp-init), Algorithm 6), the CP model behind
+gradient-descent and ALS CPD (Sec. 2.2), TEW-eq/TS (Sec. 3.1, 3.2;
+Algorithms 1, 3) and TTV/TTM (Sec. 3.3, 3.4; Algorithms 4, 5).
 """
 from __future__ import annotations
 
