@@ -60,6 +60,22 @@ def test_sweeps_match_oracle(name, nnz, dims, R):
     X.close()
 
 
+@pytest.mark.parametrize("R", [4, 12, 30, 32, 48, 64, 100, 128])
+def test_ranks_match_oracle(R):
+    """Each rank regime of the row product and the Gram kernel: R <= 32 with
+    R a multiple of 4 (W in registers), other R <= 32, R <= 64 (several row
+    groups per staged batch), and R > 64 (one thread per Gram tile)."""
+    wl, X, idx, val, Ud, Uh = _setup("uniform3d_200", 40_000, (600, 500, 400), R, seed=R)
+    lam, fit = pasta.cp_als_sweep(X, Ud)
+    Uh, lam_h, fit_h = oracle.cp_als_sweep(wl.dims, idx, val, Uh)
+    for k in range(wl.order):
+        err = G.rel_err(Ud[k].cpu().numpy(), Uh[k])
+        assert err < ALS_TOL, (R, k, err)
+    assert G.rel_err(lam.cpu().numpy(), lam_h) < ALS_TOL
+    assert abs(float(fit) - fit_h) < FIT_TOL, (float(fit), fit_h)
+    X.close()
+
+
 def test_fit_is_monotone():
     wl, X, idx, val, Ud, Uh = _setup("zipf3d", 200_000, (3_000, 2_000, 1_000), 16, seed=7)
     fits = [float(pasta.cp_als_sweep(X, Ud)[1]) for _ in range(8)]
