@@ -136,13 +136,26 @@ __global__ void __launch_bounds__(kThreads) k_fiber_write(FiberView v, const uin
 }
 
 // TTV: y(f) = sum over fiber f of val * v(i_n).  Each warp takes a chunk of
-// kTtvChunk consecutive entries in rounds of 32; per round a segmented
-// inclusive scan over lanes (fiber ids are non-decreasing) sums each
-// fiber's entries, the fiber still open at lane 31 is carried into the next
-// round, and a finished fiber is stored plainly if it lies wholly inside the
-// chunk, else added atomically (the chunk's first and last fibers may be
-// shared with the neighbouring chunks).  y must be zero-filled.
-constexpr int kTtvChunk = 1024;
+// kTtvChunk consecutive entries in rounds of 128: lane l holds entries
+// 4l .. 4l + 3 of the round (16-byte loads of fid, i_n and val; the next
+// round's are loaded while this one is summed).  Fiber ids are
+// non-decreasing, so each lane first sums its own entries fiber by fiber:
+// fibers that begin and end inside the lane are complete; the lane's first
+// fiber (head) may continue from the lanes before it and its last (tail)
+// into the lanes after it.  A segmented inclusive scan over the lanes'
+// tail sums then joins the pieces, and the fiber open at lane 31 is carried
+// into the next round.  A complete fiber is stored plainly unless it is the
+// chunk's first or last fiber (those may be shared with the neighbouring
+// chunks), which is added atomically.  y must be zero-filled.
+constexpr int kTtvChunk = 2048;
+
+template <typename A>
+__device__ __forceinline__ void ttv_put(A *y, uint32_t f, A x, uint32_t first_f, uint32_t last_f) {
+    if (f == first_f || f == last_f)
+        atomicAdd(&y[f], x);
+    else
+        y[f] = x;
+}
 
 template <typename T, typename A>
 __global__ void __launch_bounds__(256) k_ttv(const uint32_t *fid, const uint32_t *in, const float *val,
@@ -152,56 +165,90 @@ __global__ void __launch_bounds__(256) k_ttv(const uint32_t *fid, const uint32_t
     const uint64_t c0 = warp * kTtvChunk;
     if (c0 >= nnz) return;
     const uint64_t c1 = min(nnz, c0 + kTtvChunk);
-    uint32_t carry_f = kNoRow;
+    const uint32_t first_f = fid[c0], last_f = fid[c1 - 1];
+    // arrays are padded to a multiple of 4 entries, so a 16-byte load at a
+    // position below nnz stays inside them; entries at or past c1 are masked
+    uint4 nf, ni;
+    float4 nv;
+    auto load = [&](uint64_t r0) {
+        const uint64_t p = r0 + 4 * (uint64_t)lane;
+        if (p < c1) {
+            nf = *reinterpret_cast<const uint4 *>(fid + p);
+            ni = *reinterpret_cast<const uint4 *>(in + p);
+            nv = *reinterpret_cast<const float4 *>(val + p);
+        }
+    };
+    load(c0);
+    uint32_t carry_f = kNoRow;  // fiber open at the end of the previous round
     A carry_t = 0;
-    bool carry_first = true;  // the carried fiber began at the chunk's first entry
-    for (uint64_t r0 = c0; r0 < c1; r0 += 32) {
-        const uint64_t p = r0 + lane;
-        const bool ok = p < c1;
-        const uint32_t f = ok ? fid[p] : kNoRow;
-        A t = ok ? (A)val[p] * (A)v[in[p]] : (A)0;
-        const bool cont = (lane == 0) && f == carry_f;  // continues the carried fiber
-        if (carry_f != kNoRow) {  // warp-uniform
-            // the carried fiber ended with the previous round: write it
-            const uint32_t f0 = __shfl_sync(FULL, f, 0);
-            if (lane == 0 && f0 != carry_f) {
-                if (carry_first)
-                    atomicAdd(&y[carry_f], carry_t);
-                else
-                    y[carry_f] = carry_t;
+    for (uint64_t r0 = c0; r0 < c1; r0 += 128) {
+        const uint64_t p = r0 + 4 * (uint64_t)lane;
+        uint32_t f[4] = {nf.x, nf.y, nf.z, nf.w};
+        const uint32_t ix[4] = {ni.x, ni.y, ni.z, ni.w};
+        const float xv[4] = {nv.x, nv.y, nv.z, nv.w};
+        const bool last_round = r0 + 128 >= c1;
+        if (!last_round) load(r0 + 128);
+        A t[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const bool ok = p + k < c1;
+            if (!ok) f[k] = kNoRow;  // masked entries form a trailing pseudo-fiber, never written
+            t[k] = ok ? (A)xv[k] * (A)v[ix[k]] : (A)0;
+        }
+        // this lane's entries, fiber by fiber
+        const uint32_t hf = f[0], tf = f[3];
+        A run = t[0], head = 0;
+        bool whole = true;  // all four entries in one fiber
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            if (f[k] != f[k - 1]) {
+                if (whole) {
+                    head = run;
+                    whole = false;
+                } else if (f[k - 1] != kNoRow) {
+                    ttv_put(y, f[k - 1], run, first_f, last_f);  // begins and ends in this lane
+                }
+                run = t[k];
+            } else {
+                run += t[k];
             }
         }
-        if (cont) t += carry_t;
-        // segmented inclusive scan over lanes with equal fiber id
+        if (lane == 0 && carry_f != kNoRow) {
+            if (carry_f == hf) {  // continues the fiber open at the previous round's end
+                if (whole)
+                    run += carry_t;
+                else
+                    head += carry_t;
+            } else {  // that fiber ended with the previous round
+                ttv_put(y, carry_f, carry_t, first_f, last_f);
+            }
+        }
+        // segmented inclusive scan of the tail sums over lanes; a lane starts
+        // a segment unless it is wholly inside the previous lane's tail fiber
+        const uint32_t tf_prev = __shfl_up_sync(FULL, tf, 1);
+        bool B = lane == 0 || !whole || tf_prev != tf;
+        A S = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            const A tp = __shfl_up_sync(FULL, t, o);
-            const uint32_t fp = __shfl_up_sync(FULL, f, o);
-            if (lane >= o && fp == f) t += tp;
+            const A Sp = __shfl_up_sync(FULL, S, o);
+            const bool Bp = __shfl_up_sync(FULL, (int)B, o) != 0;
+            if (lane >= o) {
+                if (!B) S += Sp;
+                B = B || Bp;
+            }
         }
-        // every lane takes part in each shuffle and ballot (none is short-circuited)
-        const uint32_t fnext = __shfl_down_sync(FULL, f, 1);
-        const uint32_t fprev = __shfl_up_sync(FULL, f, 1);
-        const bool cont0 = __shfl_sync(FULL, (int)cont, 0) != 0;
-        const bool last_in_round = ok && (lane == 31 || fnext != f || r0 + lane + 1 >= c1);
-        // first lane of this lane's segment within the round
-        const unsigned starts = __ballot_sync(FULL, ok && (lane == 0 || fprev != f));
-        const int seg0 = 31 - __clz(starts & ((2u << lane) - 1u));
-        const bool seg_from_carry = (seg0 == 0) && cont0;
-        const bool seg_first = (r0 == c0 && seg0 == 0) || (seg_from_carry && carry_first);
-        const bool open = last_in_round && lane == 31 && r0 + 32 < c1;  // may continue next round
-        if (last_in_round && !open) {
-            const bool chunk_last = (p + 1 == c1);  // may continue in the next chunk
-            if (seg_first || chunk_last)
-                atomicAdd(&y[f], t);
-            else
-                y[f] = t;
+        const A S_prev = __shfl_up_sync(FULL, S, 1);
+        const uint32_t hf_next = __shfl_down_sync(FULL, hf, 1);
+        if (!whole) {
+            if (lane > 0 && tf_prev == hf) head += S_prev;
+            if (hf != kNoRow) ttv_put(y, hf, head, first_f, last_f);
         }
-        // carry the fiber open at lane 31 into the next round
-        carry_f = __shfl_sync(FULL, open ? f : kNoRow, 31);
-        carry_t = __shfl_sync(FULL, t, 31);
-        const bool first31 = __shfl_sync(FULL, (int)seg_first, 31) != 0;
-        carry_first = (carry_f != kNoRow) && first31;
+        // the tail is complete unless the next lane continues it (lane 31:
+        // unless the next round may)
+        const bool tail_done = lane < 31 ? hf_next != tf : last_round;
+        if (tail_done && tf != kNoRow) ttv_put(y, tf, S, first_f, last_f);
+        carry_f = __shfl_sync(FULL, tf, 31);
+        carry_t = __shfl_sync(FULL, S, 31);
     }
 }
 
