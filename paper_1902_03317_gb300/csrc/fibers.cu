@@ -384,7 +384,7 @@ pasta_status launch_ttm(pasta_coo_s *X, int n, const void *U, pasta_dtype dt, in
     vc.val = c.val;
     vc.present = true;
     const void *Us[2] = {nullptr, U};
-    return launch_mttkrp(&V, vc, Us, dt, 0, R, Y, s);
+    return launch_mttkrp(&V, vc, Us, dt, 0, R, Y, s, /*every_row_touched=*/true);
 }
 
 }  // namespace pasta

@@ -126,8 +126,12 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t stream);
 // Computes the mode's sorted-copy permutation if the sort left it out.
 pasta_status ensure_perm(pasta_coo_s *X, int mode, cudaStream_t stream);
 
+// every_row_touched: every row of M has at least one entry (the TTM view,
+// whose rows are fibers), so the streaming kernel's output needs zeros only
+// where it adds atomically instead of a full clear.
 pasta_status launch_mttkrp(const pasta_coo_s *X, const StoredCopy &c, const void *const *U,
-                           pasta_dtype dt, int mode, int R, void *M, cudaStream_t stream);
+                           pasta_dtype dt, int mode, int R, void *M, cudaStream_t stream,
+                           bool every_row_touched = false);
 
 // Streaming kernels (stream.cu and its per-kind units): one launch over a stored copy with the modes
 // rotated so that position 0 is the copy's sorted mode.
@@ -150,6 +154,8 @@ struct StreamLaunch {
 // kinds need order >= 3, MTTKRP (min_order 2) also takes order 2.
 bool stream_supported(pasta_dtype dt, int order, int R, const void *const *U, int skip,
                       const void *out, int min_order = 3);
+// Entries per group tile of the streaming kernels for rank R and factor type dt.
+uint32_t stream_group_tile(int R, pasta_dtype dt);
 // kind: 0 MTTKRP, 1 loss forward, 2 loss backward (one mode)
 pasta_status launch_stream(int kind, const StreamLaunch &l, cudaStream_t s);
 

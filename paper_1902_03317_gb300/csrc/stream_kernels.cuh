@@ -15,7 +15,8 @@
 // one output row are contiguous.  Each group keeps the running row sum in
 // registers.  A run that opens and closes inside its group tile is the whole
 // row: one plain 16-byte store per lane.  The first closed run of a group tile
-// (it may have begun in an earlier tile) is added with red.global.add.v4.f32;
+// is added with red.global.add.v4.f32 if it began in an earlier tile (the
+// entry before the tile has the same row), else stored as a whole row;
 // the run still open at the tile end goes to a shared-memory slot, and after
 // the warp's group tiles equal rows among its slots are summed and added
 // once.  A row spanning many tiles thus costs one atomic per warp tile (G
@@ -107,7 +108,7 @@ template <int VEC>
 struct GroupState {
     float acc[VEC];
     uint32_t cur;   // row of the open run (kNoRow before the first entry)
-    bool first;     // the open run began at the tile start
+    bool first;     // the open run continues a run of the previous tile
     uint4 row0;     // loss kinds: position-0 factor row of the open run
     float sq32;     // loss fwd: FP32 sum of squared residuals of the current chunk
     double sq;      // loss fwd: FP64 sum of the chunk sums
@@ -126,9 +127,8 @@ struct Ctx {
     float g_scale;
 };
 
-// Close the open run: the first closed run of a tile may continue a run of an
-// earlier tile and is added atomically; a later one is a whole row and is
-// stored.
+// Close the open run: a run continuing one of the previous tile (only the
+// tile's first) is added atomically; any other is a whole row and is stored.
 template <typename T, int N, int KIND>
 __device__ __forceinline__ void close_run(const Ctx<T, N, KIND> &c,
                                           GroupState<Ctx<T, N, KIND>::VEC> &s) {
@@ -324,7 +324,8 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) s.acc[e] = 0.f;
         s.cur = kNoRow;
-        s.first = true;
+        // the tile's first run continues a run of the previous tile
+        s.first = t0 > 0 && t0 < a.nnz && a.idx[0][t0 - 1] == a.idx[0][t0];
 
 
         auto issue = [&](int ci, int stage) {

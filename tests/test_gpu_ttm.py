@@ -12,7 +12,7 @@ import torch
 
 import oracle
 import paper_1902_03317_gb300 as pasta
-from paper_1902_03317_gb300 import synth
+from paper_1902_03317_gb300 import _lib, synth
 from tests import _gpu as G
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +64,29 @@ def test_ttv_matches_oracle(name, nnz, dims):
             tol = 1e-12 if dtype == torch.float64 else G.FP32_TOL
             assert G.rel_err(y.cpu().numpy(), ref) < tol, (name, n, dtype)
             assert pasta.fibers(X, n) == ref.shape[0]
+    X.close()
+
+
+@pytest.mark.parametrize("name,nnz,dims", CASES[:3])
+def test_ttm_writes_every_output_element(name, nnz, dims):
+    """TTM clears only the rows it adds into atomically (rows open at a
+    group-tile end) and stores every other fiber's row whole, so an output
+    buffer full of NaN must come back fully overwritten, equal to the oracle.
+    zipf4d keeps duplicate coordinates: fibers long enough to span tiles."""
+    wl, X, idx, val = _tensor(name, nnz, dims)
+    L = _lib.lib()
+    for n in range(wl.order):
+        for R in (32, 8):
+            U = torch.randn(wl.dims[n], R, device=G.DEV)
+            nf = pasta.fibers(X, n)
+            Y = torch.full((nf, R), float("nan"), device=G.DEV)
+            st = L.pasta_ttm(X.handle, n, U.data_ptr(), pasta.api.pasta_dtype(U.dtype), R, Y.data_ptr(),
+                             torch.cuda.current_stream().cuda_stream)
+            _lib.check(st, "pasta_ttm")
+            got = Y.cpu().numpy()
+            assert not np.isnan(got).any(), (name, n, R)
+            _, ref = oracle.ttm(wl.dims, idx, val, U.double().cpu().numpy(), n)
+            assert G.rel_err(got, ref) < G.FP32_TOL, (name, n, R)
     X.close()
 
 
