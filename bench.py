@@ -539,7 +539,7 @@ def e2e(pasta, synth, wl, dev, args, world):
     X.close()
     del Ms, Us
     mark("destroy", t)
-    steps = max(2, min(args.steps, 5))
+    steps = max(2, min(args.steps, 10))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     per_step = []
