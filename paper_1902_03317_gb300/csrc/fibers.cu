@@ -10,15 +10,17 @@
 //
 // Built in three launches: per-tile head counts (a head is a position whose
 // fiber coordinates differ from its predecessor's), one block scanning the
-// tile counts, and a pass that ranks the heads inside each tile (warp ballots,
-// rounds of 256 positions) to write fid and the head coordinates.
+// tile counts, and a pass that ranks the heads inside each tile (a lane takes
+// four consecutive positions with 16-byte loads; per round of 1024 positions a
+// warp scan of the lanes' head counts plus the block's warp totals) to write
+// fid and the head coordinates.
 //
 // With the table, Y = X x_n U is exactly an MTTKRP of the order-2 tensor with
 // coordinates (fid, i_n) and the same values: Y(f, r) = sum_{p in f}
 // val(p) U(i_n(p), r), and fid is non-decreasing along the copy.  So TTM runs
 // the MTTKRP kernels on that two-mode view.  TTV (R = 1) has its own kernel
 // (k_ttv): with one value per entry the MTTKRP lane layout idles, and fibers
-// are short, so a warp-wide segmented scan per 32 entries does the work.
+// are short, so each lane sums four entries and a warp scan joins them.
 #include <algorithm>
 
 #include "pasta_internal.cuh"
@@ -27,8 +29,9 @@ namespace pasta {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kItems = 16;
+constexpr int kItems = 16;  // positions per thread per tile
 constexpr int kTile = kThreads * kItems;
+constexpr int kRounds = kItems / 4;  // a lane takes 4 consecutive positions per round
 constexpr unsigned FULL = 0xFFFFFFFFu;
 
 struct FiberView {
@@ -41,30 +44,54 @@ struct FiberCoords {
     uint32_t *idx[kMaxOrder];  // nfibs each, same positions as FiberView
 };
 
-__device__ __forceinline__ bool is_head(const FiberView &v, uint64_t p) {
-    if (p == 0) return true;
-    bool h = false;
+// Head flags of the four positions p .. p + 3 held by this lane (p = q0 + 4
+// lane, q0 the warp's first position of the round, q0 < nnz so the whole
+// warp calls this together): bit e is set when position p + e < nnz has fiber
+// coordinates that differ from its predecessor's (position 0 is a head).
+// The lane's N-1 coordinate quads are left in w (16-byte loads: the arrays
+// are padded to a multiple of kPadEntries, so a quad starting below nnz is
+// inside them); a lane's first predecessor is the previous lane's last
+// position, and lane 0 loads its own.
+__device__ __forceinline__ unsigned head_quad(const FiberView &v, uint64_t q0, uint4 *w) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t p = q0 + 4 * (uint64_t)lane;
+    const bool live = p < v.nnz;
+    unsigned diff = 0;  // bit e: position p + e differs from its predecessor
 #pragma unroll
-    for (int j = 0; j < kMaxOrder; ++j)
-        if (j < v.nm) h |= v.idx[j][p] != v.idx[j][p - 1];
-    return h;
+    for (int j = 0; j < kMaxOrder - 1; ++j) {
+        if (j < v.nm) {
+            w[j] = live ? *reinterpret_cast<const uint4 *>(v.idx[j] + p) : make_uint4(0u, 0u, 0u, 0u);
+            uint32_t prev = __shfl_up_sync(FULL, w[j].w, 1);
+            if (lane == 0) prev = q0 > 0 ? v.idx[j][q0 - 1] : ~w[j].x;
+            diff |= (unsigned)(w[j].x != prev) | ((unsigned)(w[j].y != w[j].x) << 1) |
+                    ((unsigned)(w[j].z != w[j].y) << 2) | ((unsigned)(w[j].w != w[j].z) << 3);
+        }
+    }
+    if (p == 0) diff |= 1u;
+    const uint64_t left = live ? v.nnz - p : 0;  // positions of the quad below nnz
+    const unsigned valid = left >= 4 ? 0xFu : (1u << left) - 1u;
+    return diff & valid;
 }
 
-// counts[t] = heads in tile t (positions t * kTile + round * 256 + thread).
+// counts[t] = heads in tile t (kTile positions: kRounds rounds of 1024, a
+// warp taking 128 consecutive positions of a round, a lane 4 of them).
 __global__ void __launch_bounds__(kThreads) k_fiber_count(FiberView v, uint32_t *counts) {
     __shared__ uint32_t ws[kThreads / 32];
+    const int warp = threadIdx.x >> 5;
     const uint64_t base = (uint64_t)blockIdx.x * kTile;
     uint32_t c = 0;
-    for (int r = 0; r < kItems; ++r) {
-        const uint64_t p = base + (uint64_t)r * kThreads + threadIdx.x;
-        if (p < v.nnz && is_head(v, p)) ++c;
+    uint4 w[kMaxOrder - 1];
+    for (int r = 0; r < kRounds; ++r) {
+        const uint64_t q0 = base + (uint64_t)r * (kThreads * 4) + (uint64_t)warp * 128;
+        if (q0 >= v.nnz) break;  // warp-uniform
+        c += __popc(head_quad(v, q0, w));
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(FULL, c, o);
-    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+    if ((threadIdx.x & 31) == 0) ws[warp] = c;
     __syncthreads();
     if (threadIdx.x == 0) {
         uint32_t t = 0;
-        for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
+        for (int i = 0; i < kThreads / 32; ++i) t += ws[i];
         counts[blockIdx.x] = t;
     }
 }
@@ -105,33 +132,58 @@ __global__ void __launch_bounds__(1024) k_scan_counts(const uint32_t *counts, ui
     if (threadIdx.x == 0) *total = carry;
 }
 
-// fid[p] = (heads at or before p) - 1; each head writes its fiber's coordinates.
+// fid[p] = (heads at or before p) - 1, written as 16-byte quads (zeros past
+// nnz); each head writes its fiber's coordinates.  Same position layout as
+// k_fiber_count; heads are ranked per round by a warp scan of the lanes'
+// head counts and the block's warp totals.
 __global__ void __launch_bounds__(kThreads) k_fiber_write(FiberView v, const uint32_t *offsets,
                                                           uint32_t *fid, FiberCoords out) {
     __shared__ uint32_t wsum[kThreads / 32];
-    __shared__ uint32_t running;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint64_t base = (uint64_t)blockIdx.x * kTile;
-    if (threadIdx.x == 0) running = offsets[blockIdx.x];
-    __syncthreads();
-    for (int r = 0; r < kItems; ++r) {
-        const uint64_t p = base + (uint64_t)r * kThreads + threadIdx.x;
-        const bool h = p < v.nnz && is_head(v, p);
-        const unsigned bal = __ballot_sync(FULL, h);
-        if (lane == 0) wsum[warp] = __popc(bal);
-        __syncthreads();
-        uint32_t before = running;
-        for (int w = 0; w < warp; ++w) before += wsum[w];
-        const uint32_t incl = before + __popc(bal & ((2u << lane) - 1u));  // heads up to p in this round
-        if (p < v.nnz) {
-            fid[p] = incl - 1u;
-            if (h)
-                for (int j = 0; j < v.nm; ++j) out.idx[j][incl - 1u] = v.idx[j][p];
+    uint32_t running = offsets[blockIdx.x];  // heads before this round
+    uint4 w[kMaxOrder - 1];
+    for (int r = 0; r < kRounds; ++r) {
+        const uint64_t r0 = base + (uint64_t)r * (kThreads * 4);
+        if (r0 >= v.nnz) break;  // block-uniform
+        const uint64_t q0 = r0 + (uint64_t)warp * 128;
+        const unsigned m = q0 < v.nnz ? head_quad(v, q0, w) : 0u;
+        const uint32_t c = __popc(m);
+        uint32_t inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, inc, o);
+            if (lane >= o) inc += y;
         }
+        if (lane == 31) wsum[warp] = inc;
         __syncthreads();
-        if (threadIdx.x == 0)
-            for (int w = 0; w < kThreads / 32; ++w) running += wsum[w];
-        __syncthreads();
+        uint32_t before = running, round_total = 0;
+        for (int i = 0; i < kThreads / 32; ++i) {
+            if (i < warp) before += wsum[i];
+            round_total += wsum[i];
+        }
+        const uint64_t p = q0 + 4 * (uint64_t)lane;
+        if (p < v.nnz) {
+            uint32_t k = before + inc - c;  // heads before this lane's quad
+            uint32_t f[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                if ((m >> e) & 1u) {
+#pragma unroll
+                    for (int j = 0; j < kMaxOrder - 1; ++j) {
+                        if (j < v.nm) {
+                            const uint32_t x = e == 0 ? w[j].x : e == 1 ? w[j].y : e == 2 ? w[j].z : w[j].w;
+                            out.idx[j][k] = x;
+                        }
+                    }
+                    ++k;
+                }
+                f[e] = p + e < v.nnz ? k - 1u : 0u;
+            }
+            *reinterpret_cast<uint4 *>(fid + p) = make_uint4(f[0], f[1], f[2], f[3]);
+        }
+        running += round_total;
+        __syncthreads();  // wsum is rewritten next round
     }
 }
 
@@ -305,7 +357,11 @@ pasta_status build_fibers(pasta_coo_s *X, int n, cudaStream_t s) {
     uint32_t *offsets = reinterpret_cast<uint32_t *>(blk + fid_b + cnt_b);
     uint64_t *total = reinterpret_cast<uint64_t *>(blk + fid_b + 2 * cnt_b);
     uint64_t nfibs = 0;
-    e = cudaMemsetAsync(F.fid, 0, fid_b, s);
+    {
+        // zero tail of fid: k_fiber_write writes every quad that starts below nnz
+        const size_t written = (size_t)((X->nnz + 3) / 4) * 16;
+        e = cudaMemsetAsync(reinterpret_cast<char *>(F.fid) + written, 0, fid_b - written, s);
+    }
     if (e == cudaSuccess && X->nnz > 0) {
         k_fiber_count<<<ntiles, kThreads, 0, s>>>(v, counts);
         k_scan_counts<<<1, 1024, 0, s>>>(counts, ntiles, offsets, total);
