@@ -54,7 +54,7 @@ extern "C" {
 #define PASTA_MAX_ORDER 8
 #define PASTA_MAX_RANK 256
 #define PASTA_ALS_MAX_RANK 128
-#define PASTA_VERSION 2
+#define PASTA_VERSION 3
 
 typedef struct pasta_coo_s *pasta_coo; /* opaque, owned by the library */
 
@@ -325,6 +325,25 @@ pasta_status pasta_convert_scaled(const void *d_src, pasta_dtype src_dtype, void
  */
 pasta_status pasta_cp_als_sweep(pasta_coo X, float *const *d_U, int R, double *d_lambda,
                                 double *d_fit, void *stream);
+
+/*
+ * pasta_cp_als -- CP-ALS: up to max_sweeps sweeps as in pasta_cp_als_sweep,
+ * stopping early once the fits of two consecutive sweeps differ by less than
+ * tol (tol < 0: always max_sweeps).  Each factor's Gram matrix is formed once
+ * from the factors as given and afterwards kept from the pass that
+ * normalises it, so a sweep after the first skips N Gram passes.
+ *   d_U, R, d_lambda  as for pasta_cp_als_sweep (d_lambda: the last sweep's)
+ *   max_sweeps        >= 1
+ *   h_fits            host array of max_sweeps doubles: the fit after each
+ *                     sweep run (entries past *h_sweeps are left unwritten)
+ *   h_sweeps          host output: sweeps completed
+ * The call synchronises `stream` once per sweep (solve status and fit).  On
+ * PASTA_ERR_SINGULAR, *h_sweeps sweeps completed before the failing one.
+ * PASTA_ERR_INVALID_ARG for max_sweeps < 1, NULL h_fits / h_sweeps or a NaN
+ * tol; otherwise the errors of pasta_cp_als_sweep.
+ */
+pasta_status pasta_cp_als(pasta_coo X, float *const *d_U, int R, int max_sweeps, double tol,
+                          double *d_lambda, double *h_fits, int *h_sweeps, void *stream);
 
 /* Element-wise operators of TEW-eq and TS (Sec. 3.1, 3.2). */
 typedef enum {

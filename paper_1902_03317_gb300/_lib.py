@@ -49,6 +49,7 @@ SIGNATURES = {
     "pasta_cp_loss_fwd_bwd": (_I, [_P, _P, _I, _I, _P, _P, _P, _P]),
     "pasta_cp_loss_fwd_noalloc": (_I, [_I, _P, _U64, _P, _P, _P, _I, _I, _P, _P, _P]),
     "pasta_cp_als_sweep": (_I, [_P, _P, _I, _P, _P, _P]),
+    "pasta_cp_als": (_I, [_P, _P, _I, _I, ctypes.c_double, _P, _P, _P, _P]),
     "pasta_tew_eq": (_I, [_P, _P, _I, _P, _P]),
     "pasta_ts": (_I, [_P, _I, ctypes.c_double, _P, _P]),
     "pasta_coo_fibers": (_I, [_P, _I, _P, _P]),

@@ -419,24 +419,29 @@ def cp_als_sweep(X: CooTensor, Us: Sequence[torch.Tensor], want_fit: bool = True
 
 def cp_als(X: CooTensor, R: int, max_sweeps: int = 50, tol: float = 1e-5,
            init: Sequence[torch.Tensor] | None = None, seed: int = 0):
-    """CP decomposition by alternating least squares: sweeps until the fit
-    changes by less than ``tol`` or ``max_sweeps`` is reached.  ``init``
-    defaults to N(0, 1) factors drawn on the device from ``seed``.  Returns
-    ``(Us, lam, fits)`` with the fit after each sweep (one host read per
-    sweep)."""
+    """CP decomposition by alternating least squares (pasta_cp_als): sweeps
+    until the fit changes by less than ``tol`` or ``max_sweeps`` is reached
+    (``tol < 0``: always ``max_sweeps``).  ``init`` defaults to N(0, 1)
+    factors drawn on the device from ``seed``.  Returns ``(Us, lam, fits)``
+    with the fit after each sweep run."""
     if init is None:
         g = torch.Generator(device=X.device).manual_seed(seed)
         Us = [torch.randn((d, R), generator=g, device=X.device, dtype=torch.float32) for d in X.dims]
     else:
         Us = [u.detach().to(device=X.device, dtype=torch.float32).contiguous().clone() for u in init]
-    fits: list[float] = []
-    lam = None
-    for _ in range(max_sweeps):
-        lam, fit = cp_als_sweep(X, Us)
-        fits.append(float(fit))
-        if len(fits) > 1 and abs(fits[-1] - fits[-2]) < tol:
-            break
-    return Us, lam, fits
+    X.sort_all()
+    for k, U in enumerate(Us):
+        if tuple(U.shape) != (X.dims[k], R):
+            raise ValueError(f"U[{k}] must be {X.dims[k]} x {R}")
+    lam = torch.empty(R, dtype=torch.float64, device=X.device)
+    fits = (ctypes.c_double * max(1, int(max_sweeps)))()
+    done = ctypes.c_int(0)
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_cp_als(X.handle, _lib.ptr_array([U.data_ptr() for U in Us]), int(R), int(max_sweeps),
+                                     float(tol), lam.data_ptr(), ctypes.cast(fits, ctypes.c_void_p),
+                                     ctypes.cast(ctypes.pointer(done), ctypes.c_void_p), _stream(X.device))
+    _lib.check(st, "pasta_cp_als")
+    return Us, lam, [float(fits[i]) for i in range(done.value)]
 
 
 class CPLoss(torch.autograd.Function):

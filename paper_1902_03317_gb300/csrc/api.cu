@@ -582,8 +582,9 @@ pasta_status pasta_cp_loss_fwd_bwd(pasta_coo X, const void *const *d_U, pasta_dt
                                   static_cast<cudaStream_t>(stream));
 }
 
-pasta_status pasta_cp_als_sweep(pasta_coo X, float *const *d_U, int R, double *d_lambda,
-                                double *d_fit, void *stream) {
+namespace {
+
+pasta_status check_als(pasta_coo X, float *const *d_U, int R, const double *d_lambda) {
     pasta_status st = check_factors(X, reinterpret_cast<const void *const *>(d_U), PASTA_F32, R, -1);
     if (st != PASTA_OK) return st;
     if (R > PASTA_ALS_MAX_RANK) {
@@ -603,7 +604,28 @@ pasta_status pasta_cp_als_sweep(pasta_coo X, float *const *d_U, int R, double *d
         set_error("CP-ALS needs at least one stored entry");
         return PASTA_ERR_INVALID_ARG;
     }
-    return run_cp_als_sweep(X, d_U, R, d_lambda, d_fit, static_cast<cudaStream_t>(stream));
+    return PASTA_OK;
+}
+
+}  // namespace
+
+pasta_status pasta_cp_als_sweep(pasta_coo X, float *const *d_U, int R, double *d_lambda,
+                                double *d_fit, void *stream) {
+    const pasta_status st = check_als(X, d_U, R, d_lambda);
+    if (st != PASTA_OK) return st;
+    return run_cp_als(X, d_U, R, 1, -1.0, d_lambda, d_fit, nullptr, nullptr, static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_cp_als(pasta_coo X, float *const *d_U, int R, int max_sweeps, double tol,
+                          double *d_lambda, double *h_fits, int *h_sweeps, void *stream) {
+    const pasta_status st = check_als(X, d_U, R, d_lambda);
+    if (st != PASTA_OK) return st;
+    if (max_sweeps < 1 || !h_fits || !h_sweeps || !(tol == tol)) {
+        set_error("pasta_cp_als: need max_sweeps >= 1, h_fits, h_sweeps and a tolerance that is a number");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    return run_cp_als(X, d_U, R, max_sweeps, tol, d_lambda, nullptr, h_fits, h_sweeps,
+                      static_cast<cudaStream_t>(stream));
 }
 
 // Output handle of TEW-eq / TS: a new handle with X's coordinates, or the

@@ -25,6 +25,7 @@
 //   k_als_lambda  lam, 1 / lam and <M, U_n> per column
 //   k_als_fit     ||model||^2 = lam^T (Hadamard of all Grams) lam and the fit
 #include <algorithm>
+#include <cmath>
 
 #include "pasta_internal.cuh"
 
@@ -683,13 +684,14 @@ pasta_status rows(const float *M, uint64_t I, int R, const float *W, float *U, d
 
 }  // namespace
 
-pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *lambda, double *fit,
-                              cudaStream_t s) {
+pasta_status run_cp_als(pasta_coo_s *X, float *const *U, int R, int max_sweeps, double tol, double *lambda,
+                        double *fit, double *h_fits, int *h_sweeps, cudaStream_t s) {
     const int N = X->order;
     const int RR = R * R;
     uint64_t imax = 0;
     for (int k = 0; k < N; ++k) imax = std::max(imax, X->dims[k]);
     const int nblk = 2 * X->num_sms;  // k_gram grid cap
+    if (h_sweeps) *h_sweeps = 0;
 
     // the handle's scratch, cut into 256-byte aligned pieces
     size_t off = 0;
@@ -707,6 +709,7 @@ pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *la
     const size_t oPart = take(std::max((size_t)nblk * RR, (size_t)rows_blocks(imax, R, X->num_sms) * 2 * R) *
                               sizeof(double));
     const size_t oStatus = take(sizeof(int));
+    const size_t oFit = take(sizeof(double));
     char *base = nullptr;
     {
         void *p = nullptr;
@@ -722,55 +725,66 @@ pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *la
     double *inner = reinterpret_cast<double *>(base + oInner);
     double *part = reinterpret_cast<double *>(base + oPart);
     int *status = reinterpret_cast<int *>(base + oStatus);
+    double *fitp = fit ? fit : (h_fits ? reinterpret_cast<double *>(base + oFit) : nullptr);
 
-    auto fail = [&](pasta_status e) { return e; };
-    cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), s);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMemsetAsync(status)"));
-
+    cudaError_t e;
     // ||X||^2 once per handle (the values never change after create)
     if (!X->als_normsq) {
         e = dev_malloc(reinterpret_cast<void **>(&X->als_normsq), sizeof(double), s);
         if (e != cudaSuccess) {
             X->als_normsq = nullptr;
-            return fail(cuda_fail(e, "allocation of normsq"));
+            return cuda_fail(e, "allocation of normsq");
         }
         const int b = (int)std::max<uint64_t>(1, std::min<uint64_t>((X->nnz + 255) / 256, (uint64_t)nblk));
         k_sumsq<<<b, 256, 0, s>>>(X->orig.val, X->nnz, part);
         k_sum_parts<<<1, 256, 0, s>>>(part, b, 1, X->als_normsq);
     }
-
-    for (int k = 0; k < N; ++k) {
-        const pasta_status gs = gram(U[k], X->dims[k], R, X->num_sms, nblk, part, G + (size_t)k * RR, s);
-        if (gs != PASTA_OK) return fail(gs);
-    }
-
     const size_t solve_smem = ((size_t)RR + 5 * R + 2) * sizeof(double);
     e = cudaFuncSetAttribute(k_als_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)solve_smem);
-    if (e != cudaSuccess) return fail(cuda_fail(e, "cudaFuncSetAttribute(k_als_solve)"));
-    for (int n = 0; n < N; ++n) {
-        const uint64_t I = X->dims[n];
-        pasta_status st = launch_mttkrp(X, X->sorted[n], reinterpret_cast<const void *const *>(U),
-                                        PASTA_F32, n, R, M, s);
-        if (st != PASTA_OK) return fail(st);
-        k_als_solve<<<1, kSolveThreads, solve_smem, s>>>(G, N, n, R, W, status);
-        st = rows(M, I, R, W, U[n], part, X->num_sms, s);  // U_n = M W and its column statistics
-        if (st != PASTA_OK) return fail(st);
-        k_sum_parts<<<(2 * R + 31) / 32, 256, 0, s>>>(part, rows_blocks(I, R, X->num_sms), 2 * R, st2);
-        k_als_lambda<<<1, 128, 0, s>>>(st2, R, lambda, inv, inner);
-        st = gram(U[n], I, R, X->num_sms, nblk, part, G + (size_t)n * RR, s, inv);  // normalise + Gram
-        if (st != PASTA_OK) return fail(st);
-    }
-    if (fit) k_als_fit<<<1, 256, 0, s>>>(G, N, R, lambda, inner, X->als_normsq, fit);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(cuda_fail(e, "CP-ALS kernels"));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_als_solve)");
 
-    int h_status = 0;
-    e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "CP-ALS status read");
-    if (h_status != 0) {
-        set_error("CP-ALS: V of mode %d is singular (non-positive pivot)", h_status - 1);
-        return PASTA_ERR_SINGULAR;
+    double prev_fit = 0.0;
+    for (int it = 0; it < max_sweeps; ++it) {
+        e = cudaMemsetAsync(status, 0, sizeof(int), s);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
+        // The Gram matrices of the factors as given; later sweeps keep those
+        // formed when each factor was last normalised.
+        if (it == 0)
+            for (int k = 0; k < N; ++k) {
+                const pasta_status gs = gram(U[k], X->dims[k], R, X->num_sms, nblk, part, G + (size_t)k * RR, s);
+                if (gs != PASTA_OK) return gs;
+            }
+        for (int n = 0; n < N; ++n) {
+            const uint64_t I = X->dims[n];
+            pasta_status st = launch_mttkrp(X, X->sorted[n], reinterpret_cast<const void *const *>(U),
+                                            PASTA_F32, n, R, M, s);
+            if (st != PASTA_OK) return st;
+            k_als_solve<<<1, kSolveThreads, solve_smem, s>>>(G, N, n, R, W, status);
+            st = rows(M, I, R, W, U[n], part, X->num_sms, s);  // U_n = M W and its column statistics
+            if (st != PASTA_OK) return st;
+            k_sum_parts<<<(2 * R + 31) / 32, 256, 0, s>>>(part, rows_blocks(I, R, X->num_sms), 2 * R, st2);
+            k_als_lambda<<<1, 128, 0, s>>>(st2, R, lambda, inv, inner);
+            st = gram(U[n], I, R, X->num_sms, nblk, part, G + (size_t)n * RR, s, inv);  // normalise + Gram
+            if (st != PASTA_OK) return st;
+        }
+        if (fitp) k_als_fit<<<1, 256, 0, s>>>(G, N, R, lambda, inner, X->als_normsq, fitp);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "CP-ALS kernels");
+
+        int h_status = 0;
+        double h_fit = 0.0;
+        e = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && h_fits) e = cudaMemcpyAsync(&h_fit, fitp, sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "CP-ALS status read");
+        if (h_status != 0) {
+            set_error("CP-ALS: V of mode %d is singular (non-positive pivot)", h_status - 1);
+            return PASTA_ERR_SINGULAR;
+        }
+        if (h_fits) h_fits[it] = h_fit;
+        if (h_sweeps) *h_sweeps = it + 1;
+        if (h_fits && tol >= 0.0 && it > 0 && std::fabs(h_fit - prev_fit) < tol) break;
+        prev_fit = h_fit;
     }
     return PASTA_OK;
 }

@@ -178,9 +178,13 @@ pasta_status launch_cp_loss_fwd_bwd(const pasta_coo_s *X, const void *const *U, 
                                     int R, double *loss, const double *gscale, void *const *G,
                                     cudaStream_t stream);
 
-// One CP-ALS sweep (cp_als.cu); arguments checked by the caller.
-pasta_status run_cp_als_sweep(pasta_coo_s *X, float *const *U, int R, double *lambda, double *fit,
-                              cudaStream_t stream);
+// Up to max_sweeps CP-ALS sweeps (cp_als.cu); arguments checked by the
+// caller.  fit: device double for the last sweep's fit, or NULL; h_fits:
+// host array of max_sweeps fits, or NULL; stops early once two consecutive
+// fits differ by less than tol (tol >= 0, with h_fits); *h_sweeps = sweeps
+// completed.  Synchronises `stream` once per sweep.
+pasta_status run_cp_als(pasta_coo_s *X, float *const *U, int R, int max_sweeps, double tol, double *lambda,
+                        double *fit, double *h_fits, int *h_sweeps, cudaStream_t stream);
 
 // TEW-eq / TS (tew.cu): coordinate equality of two creation-order copies
 // (synchronises `stream`), and z = x op y (y == NULL: z = x op s) over n_pad

@@ -42,7 +42,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 
 def test_version_and_status_strings(lib):
-    assert lib.pasta_version() == 2
+    assert lib.pasta_version() == 3
     for code, name in _lib.STATUS.items():
         assert lib.pasta_status_str(code).decode() == name
 
@@ -90,3 +90,15 @@ def test_set_allocator_argument_checks():
     assert L.pasta_set_allocator(None, ctypes.cast(f, ctypes.c_void_p), None) == 1
     assert L.pasta_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None) == 0
     assert L.pasta_set_allocator(None, None, None) == 0
+
+
+def test_cp_als_rejects_a_null_handle():
+    """pasta_cp_als checks its arguments before any device work."""
+    import ctypes
+    from paper_1902_03317_gb300 import _lib
+    L = _lib.lib()
+    fits = (ctypes.c_double * 4)()
+    done = ctypes.c_int(7)
+    assert L.pasta_cp_als(None, None, 4, 4, 0.0, None, ctypes.cast(fits, ctypes.c_void_p),
+                          ctypes.cast(ctypes.pointer(done), ctypes.c_void_p), None) == 1
+    assert b"NULL" in L.pasta_last_error()

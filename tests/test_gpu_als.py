@@ -76,6 +76,53 @@ def test_ranks_match_oracle(R):
     X.close()
 
 
+def test_driver_matches_single_sweeps():
+    """pasta_cp_als keeps each factor's Gram matrix from the pass that
+    normalised it instead of re-forming it from the stored factor: the same
+    values, summed over a possibly different grid, so K sweeps of the driver
+    match K calls of the single sweep to FP rounding, and the oracle's K
+    sweeps within the sweep tolerances."""
+    wl, X, idx, val, Ud, Uh = _setup("zipf3d", 300_001, (5_000, 3_000, 2_000), 16, seed=5)
+    K = 4
+    Us1 = [u.clone() for u in Ud]
+    fits1 = [float(pasta.cp_als_sweep(X, Us1)[1]) for _ in range(K)]
+    Us2, lam2, fits2 = pasta.cp_als(X, 16, max_sweeps=K, tol=-1.0, init=Ud)
+    assert len(fits2) == K
+    np.testing.assert_allclose(fits2, fits1, rtol=0, atol=2e-6)
+    for a, b in zip(Us2, Us1):
+        assert G.rel_err(a.cpu().numpy(), b.cpu().numpy()) < 1e-5
+    Ur = Uh
+    for _ in range(K):
+        Ur, lam_r, fit_r = oracle.cp_als_sweep(wl.dims, idx, val, Ur)
+    for k in range(wl.order):
+        assert G.rel_err(Us2[k].cpu().numpy(), Ur[k]) < 10 * ALS_TOL, k
+    assert abs(fits2[-1] - fit_r) < 10 * FIT_TOL
+    X.close()
+
+
+def test_driver_arguments_and_early_stop():
+    wl, X, idx, val, Ud, Uh = _setup("uniform3d_200", 5_000, (50, 40, 30), 8)
+    # a loose tolerance stops after the second sweep
+    _, _, fits = pasta.cp_als(X, 8, max_sweeps=10, tol=1.0, init=Ud)
+    assert len(fits) == 2
+    L = _lib.lib()
+    import ctypes
+    lam = torch.empty(8, dtype=torch.float64, device=G.DEV)
+    U = [u.clone() for u in Ud]
+    ptrs = _lib.ptr_array([u.data_ptr() for u in U])
+    s = torch.cuda.current_stream().cuda_stream
+    fits_h = (ctypes.c_double * 3)()
+    done = ctypes.c_int(0)
+    fp = ctypes.cast(fits_h, ctypes.c_void_p)
+    dp = ctypes.cast(ctypes.pointer(done), ctypes.c_void_p)
+    assert L.pasta_cp_als(X.handle, ptrs, 8, 0, 0.0, lam.data_ptr(), fp, dp, s) == 1        # max_sweeps < 1
+    assert L.pasta_cp_als(X.handle, ptrs, 8, 3, 0.0, lam.data_ptr(), None, dp, s) == 1      # no h_fits
+    assert L.pasta_cp_als(X.handle, ptrs, 8, 3, float("nan"), lam.data_ptr(), fp, dp, s) == 1
+    assert L.pasta_cp_als(X.handle, ptrs, 8, 3, -1.0, lam.data_ptr(), fp, dp, s) == 0
+    assert done.value == 3 and all(0.0 < f <= 1.0 for f in fits_h)
+    X.close()
+
+
 def test_fit_is_monotone():
     wl, X, idx, val, Ud, Uh = _setup("zipf3d", 200_000, (3_000, 2_000, 1_000), 16, seed=7)
     fits = [float(pasta.cp_als_sweep(X, Ud)[1]) for _ in range(8)]
