@@ -22,6 +22,7 @@ sample of the same workload); the reference paper has no GPU code.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -553,6 +554,11 @@ def e2e(pasta, synth, wl, dev, args, world):
     mark("destroy", t)
     steps = max(2, min(args.steps, 10))
     torch.cuda.synchronize()
+    # host-timed steps: Python's cyclic garbage collector is paused while
+    # they run, as timeit does
+    gc.collect()
+    gc_was_on = gc.isenabled()
+    gc.disable()
     t0 = time.perf_counter()
     per_step = []
     for _ in range(steps):
@@ -561,6 +567,8 @@ def e2e(pasta, synth, wl, dev, args, world):
         per_step.append(round((time.perf_counter() - ts) * 1e3, 2))
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
+    if gc_was_on:
+        gc.enable()
     if world > 1:
         import torch.distributed as dist
         t = torch.tensor([dt], dtype=torch.float64)

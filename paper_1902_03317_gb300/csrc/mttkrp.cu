@@ -245,35 +245,14 @@ pasta_status by_order(const pasta_coo_s *X, const StoredCopy &c, const void *con
 
 bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Zeros the output row of the last entry of every group tile: the streaming
-// kernel adds atomically only into rows open at a group-tile end (the run
-// reaching the end, and the same row's continuation in the next tile), and
-// stores every other row whole.  One warp per tile, lanes across R.
-__global__ void __launch_bounds__(256) k_zero_tile_end_rows(const uint32_t *idx0, uint64_t nnz, uint32_t tile,
-                                                            uint32_t R, float *M) {
-    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t ntiles = (nnz + tile - 1) / tile;
-    if (w >= ntiles) return;
-    const uint64_t p = min(nnz, (w + 1) * (uint64_t)tile) - 1;
-    float *row = M + (uint64_t)idx0[p] * R;
-    for (uint32_t r = threadIdx.x & 31; r < R; r += 32) row[r] = 0.f;
-}
-
 }  // namespace
 
 pasta_status launch_mttkrp(const pasta_coo_s *X, const StoredCopy &c, const void *const *U,
                            pasta_dtype dt, int mode, int R, void *M, cudaStream_t s,
                            bool every_row_touched) {
     if (stream_supported(dt, X->order, R, U, mode, M, 2)) {
-        if (every_row_touched && X->nnz > 0) {
-            const uint32_t tile = stream_group_tile(R, dt);
-            const uint64_t ntiles = (X->nnz + tile - 1) / tile;
-            k_zero_tile_end_rows<<<(unsigned)((ntiles + 7) / 8), 256, 0, s>>>(c.idx[mode], X->nnz, tile, (uint32_t)R,
-                                                                           static_cast<float *>(M));
-            PASTA_CUDA(cudaGetLastError());
-        } else {
+        if (!every_row_touched || X->nnz == 0)
             PASTA_CUDA(cudaMemsetAsync(M, 0, (size_t)X->dims[mode] * (size_t)R * sizeof(float), s));
-        }
         if (X->nnz == 0) return PASTA_OK;
         StreamLaunch l;
         l.order = X->order;
@@ -288,6 +267,7 @@ pasta_status launch_mttkrp(const pasta_coo_s *X, const StoredCopy &c, const void
         l.out = static_cast<float *>(M);
         l.nnz = X->nnz;
         l.num_sms = X->num_sms;
+        l.zero_tile_end_rows = every_row_touched;
         return launch_stream(0, l, s);
     }
     const int es = (int)dtype_size(dt);

@@ -149,13 +149,15 @@ struct StreamLaunch {
     int num_sms = 0;
     int max_blocks = 0;          // 0 = no cap
     int *blocks_used = nullptr;  // optional
+    // MTTKRP whose every output row has an entry (the TTM view): instead of
+    // a cleared output, zero only the rows open at a group-tile end, the
+    // ones the kernel adds into atomically
+    bool zero_tile_end_rows = false;
 };
 // True when the streaming kernels cover this case (see stream.cu); the loss
 // kinds need order >= 3, MTTKRP (min_order 2) also takes order 2.
 bool stream_supported(pasta_dtype dt, int order, int R, const void *const *U, int skip,
                       const void *out, int min_order = 3);
-// Entries per group tile of the streaming kernels for rank R and factor type dt.
-uint32_t stream_group_tile(int R, pasta_dtype dt);
 // kind: 0 MTTKRP, 1 loss forward, 2 loss backward (one mode)
 pasta_status launch_stream(int kind, const StreamLaunch &l, cudaStream_t s);
 

@@ -30,11 +30,6 @@ bool stream_supported(pasta_dtype dt, int order, int R, const void *const *U, in
     return true;
 }
 
-uint32_t stream_group_tile(int R, pasta_dtype dt) {
-    const int es = (int)dtype_size(dt);
-    return (uint32_t)stream::group_tile(make_geometry(R, 16 / es, es).L);
-}
-
 pasta_status launch_stream(int kind, const StreamLaunch &l, cudaStream_t s) {
     switch (kind) {
         case stream::kMttkrp: return launch_stream_mttkrp(l, s);

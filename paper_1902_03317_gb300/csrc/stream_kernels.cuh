@@ -39,8 +39,9 @@ __host__ __device__ constexpr int ilog2(int x) { return x <= 1 ? 0 : 1 + ilog2(x
 
 enum Kind : int { kMttkrp = 0, kLossFwd = 1, kLossBwd = 2 };
 
-// Entries per lane-group tile (at least one chunk of 4L).  A block tile is
-// kWarps * G group tiles, a warp tile the warp's G of them.
+// Longest lane-group tile (at least one chunk of 4L); the launch may pick a
+// shorter multiple of the chunk to balance the grid.  A block tile is kWarps
+// * G group tiles, a warp tile the warp's G of them.
 #ifndef PASTA_STREAM_GROUP_TILE
 #define PASTA_STREAM_GROUP_TILE 512
 #endif
@@ -283,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
     const int lig = lane & (L - 1);
     const int grp = lane >> lshift;
     const int G = 32 >> lshift;
-    const int tile = LC ? group_tile(LC) : a.tile;
+    const int tile = a.tile;
     const int chunk = 4 * L;
     const int GS = 4 * L + 4;  // padded words per group chunk (bank spread)
     const int AS = G * GS;     // words per array per stage

@@ -19,6 +19,24 @@ using stream::kWarps;
 
 constexpr int kStages = 2;
 
+// Zeros the output row of the last entry of every group tile of `tile`
+// entries: the streaming kernel adds atomically only into rows open at a
+// group-tile end (the run reaching the end, and the same row's continuation
+// in the next tile) and stores every other row whole.  One warp per tile,
+// lanes across R.  (Internal linkage: every unit that includes this header
+// gets its own copy.)
+namespace {
+__global__ void __launch_bounds__(256) k_zero_tile_end_rows(const uint32_t *idx0, uint64_t nnz, uint32_t tile,
+                                                            uint32_t R, float *out) {
+    const uint64_t w = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t ntiles = (nnz + tile - 1) / tile;
+    if (w >= ntiles) return;
+    const uint64_t p = min(nnz, (w + 1) * (uint64_t)tile) - 1;
+    float *row = out + (uint64_t)idx0[p] * R;
+    for (uint32_t r = threadIdx.x & 31; r < R; r += 32) row[r] = 0.f;
+}
+}  // namespace
+
 // Blocks per SM each instantiation is compiled for (register budget
 // 65536 / (256 * blocks)), chosen by measurement on the order-3 workloads:
 // occupancy outweighs a few spilled registers, not many; higher orders need
@@ -61,17 +79,30 @@ pasta_status run(const StreamLaunch &l, cudaStream_t s) {
     if (LC != 0 && g.L != LC) return PASTA_ERR_UNSUPPORTED;  // by_lanes picks LC = L
     a.L = g.L;
     a.lshift = g.lshift;
-    a.tile = stream::group_tile(g.L);
     const size_t smem = stream::smem_bytes(N, kStages, g.L, l.R);
     auto kern = k_stream<T, N, KIND, kStages, MINB, LC, row0_late<KIND>()>;
     PASTA_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     PASTA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
     per_sm = std::max(per_sm, 1);
-    const uint64_t span = (uint64_t)a.tile * (uint64_t)(32 >> g.lshift) * kWarps;
-    const uint64_t nbt = std::max<uint64_t>(1, (l.nnz + span - 1) / span);
-    uint64_t blocks = std::min<uint64_t>(nbt, (uint64_t)l.num_sms * (uint64_t)per_sm);
+    // Block tiles go round-robin over the resident grid.  With the longest
+    // group tile the last round may leave most blocks idle, so the tile is
+    // shortened (to a multiple of the chunk) until the block tiles just fill
+    // the same number of rounds.
+    const uint64_t per_bt = (uint64_t)(32 >> g.lshift) * kWarps;  // group tiles per block tile
+    const uint64_t chunk = 4 * (uint64_t)g.L;
+    const uint64_t longest = (uint64_t)stream::group_tile(g.L);
+    const uint64_t nbt0 = std::max<uint64_t>(1, (l.nnz + longest * per_bt - 1) / (longest * per_bt));
+    uint64_t blocks = std::min<uint64_t>(nbt0, (uint64_t)l.num_sms * (uint64_t)per_sm);
     if (l.max_blocks > 0) blocks = std::min<uint64_t>(blocks, (uint64_t)l.max_blocks);
+    const uint64_t rounds = (nbt0 + blocks - 1) / blocks;
+    const uint64_t need = (l.nnz + blocks * rounds * per_bt - 1) / (blocks * rounds * per_bt);
+    a.tile = (int)std::min<uint64_t>(longest, std::max<uint64_t>(chunk, (need + chunk - 1) / chunk * chunk));
+    if (l.zero_tile_end_rows) {
+        const uint64_t ntiles = (l.nnz + a.tile - 1) / a.tile;
+        k_zero_tile_end_rows<<<(unsigned)((ntiles + 7) / 8), 256, 0, s>>>(l.idx[0], l.nnz, (uint32_t)a.tile,
+                                                                       (uint32_t)l.R, l.out);
+    }
     kern<<<(int)blocks, kThreads, smem, s>>>(a);
     PASTA_CUDA(cudaGetLastError());
     if (l.blocks_used) *l.blocks_used = (int)blocks;
