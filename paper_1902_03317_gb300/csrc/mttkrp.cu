@@ -218,12 +218,9 @@ pasta_status run(const pasta_coo_s *X, const StoredCopy &c, const void *const *U
     PASTA_CUDA(cudaMemsetAsync(M, 0, (size_t)X->dims[mode] * (size_t)R * sizeof(A), s));
     if (X->nnz == 0) return PASTA_OK;
 
-    static int per_sm = 0;
-    if (per_sm == 0) {
-        PASTA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mttkrp<T, VEC, J, NM>,
-                                                                 kThreads, 0));
-        if (per_sm < 1) per_sm = 1;
-    }
+    int per_sm = 0;  // queried per call: no shared state between host threads
+    PASTA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mttkrp<T, VEC, J, NM>, kThreads, 0));
+    if (per_sm < 1) per_sm = 1;
     const uint64_t G = 32u >> g.lshift;
     const uint64_t nwt = (X->nnz + (uint64_t)g.tile * G - 1) / ((uint64_t)g.tile * G);
     const uint64_t wpb = kThreads / 32;
