@@ -41,20 +41,45 @@ struct KeySpec {
 };
 
 // keys[m] = the key of entry m; payload[m] = its value's bits (payload_val)
-// or its creation-order number.
+// or its creation-order number.  A thread takes four consecutive entries:
+// 16-byte loads of each index array and the values (stored arrays are
+// 16-byte aligned and padded past nnz), 16-byte stores where all four are
+// real entries.
 __global__ void k_make_keys(CooView v, KeySpec ks, uint64_t *keys, uint32_t *payload, bool payload_val) {
-    for (uint64_t m = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; m < v.nnz;
-         m += (uint64_t)gridDim.x * blockDim.x) {
-        uint64_t key = 0;
+    const uint64_t n4 = (v.nnz + 3) / 4;
+    for (uint64_t q = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n4; q += (uint64_t)gridDim.x * blockDim.x) {
+        const uint64_t m = 4 * q;
+        uint64_t key[4] = {0, 0, 0, 0};
 #pragma unroll
         for (int p = 0; p < kMaxOrder; ++p) {
             if (p < ks.order && ks.use[p]) {
-                const uint64_t ix = v.idx[ks.mode[p]][m];
-                key |= (ix >> ks.shr[p]) << ks.shl[p];
+                const uint4 ix = *reinterpret_cast<const uint4 *>(v.idx[ks.mode[p]] + m);
+                key[0] |= ((uint64_t)ix.x >> ks.shr[p]) << ks.shl[p];
+                key[1] |= ((uint64_t)ix.y >> ks.shr[p]) << ks.shl[p];
+                key[2] |= ((uint64_t)ix.z >> ks.shr[p]) << ks.shl[p];
+                key[3] |= ((uint64_t)ix.w >> ks.shr[p]) << ks.shl[p];
             }
         }
-        keys[m] = ks.final_shift >= 64 ? 0 : (key >> ks.final_shift);
-        payload[m] = payload_val ? __float_as_uint(v.val[m]) : (uint32_t)m;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) key[e] = ks.final_shift >= 64 ? 0 : (key[e] >> ks.final_shift);
+        uint4 pl;
+        if (payload_val) {
+            const float4 x = *reinterpret_cast<const float4 *>(v.val + m);
+            pl = make_uint4(__float_as_uint(x.x), __float_as_uint(x.y), __float_as_uint(x.z), __float_as_uint(x.w));
+        } else {
+            pl = make_uint4((uint32_t)m, (uint32_t)m + 1u, (uint32_t)m + 2u, (uint32_t)m + 3u);
+        }
+        if (m + 3 < v.nnz) {
+            reinterpret_cast<ulonglong2 *>(keys + m)[0] = make_ulonglong2(key[0], key[1]);
+            reinterpret_cast<ulonglong2 *>(keys + m)[1] = make_ulonglong2(key[2], key[3]);
+            *reinterpret_cast<uint4 *>(payload + m) = pl;
+        } else {
+            const uint32_t pv[4] = {pl.x, pl.y, pl.z, pl.w};
+            for (int e = 0; e < 4 && m + e < v.nnz; ++e) {
+                keys[m + e] = key[e];
+                payload[m + e] = pv[e];
+            }
+        }
     }
 }
 
