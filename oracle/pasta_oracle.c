@@ -7,7 +7,7 @@
  * CUDA library: it is a plain, slow, single-threaded restatement of the
  * definitions, written so that a reader can check it against the paper by eye.
  *
- * Conventions (readings of the paper, each also listed in the design doc):
+ * Conventions (readings of the paper):
  *   - COO storage (Sec. 5.1): one index array per mode ("inds") and one value
  *     array ("val"), both of length nnz; indices are 0-based (the Sec. 5.1
  *     example names entries (1,0,0) and (1,0,2) of a 4x4x3 tensor).
