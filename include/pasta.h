@@ -419,6 +419,21 @@ pasta_status pasta_ttv(pasta_coo X, int mode, const void *d_v, pasta_dtype v_dty
                        void *stream);
 
 /*
+ * pasta_set_grid_cap -- upper bound on the thread blocks of every MTTKRP and
+ * CP-loss launch (streaming and general kernels; TTM, which runs as an
+ * MTTKRP, included); 0 (the default) removes it.  Not a paper operation: a
+ * diagnostic.  The kernels stride over the stored entries with whatever grid
+ * they get, so results do not depend on it beyond FP32 rounding; a small cap
+ * makes each block walk many block tiles in turn, which lets small inputs
+ * exercise the same multi-round path that large ones take with the full grid.
+ * Process-wide (all host threads and devices); it applies to launches made
+ * after the call.  PASTA_ERR_INVALID_ARG for max_blocks < 0.
+ * pasta_get_grid_cap returns the current cap.
+ */
+pasta_status pasta_set_grid_cap(int max_blocks);
+int pasta_get_grid_cap(void);
+
+/*
  * Device memory of the library's own buffers (stored copies, scratch, fiber
  * tables, partial sums).  By default cudaMalloc/cudaFree; a caller with its
  * own caching allocator (a framework's) can route them through it, so that

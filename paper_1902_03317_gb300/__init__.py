@@ -7,10 +7,10 @@ and a thin torch-facing API.  Nothing here computes on the CPU: if the
 library is missing, calls fail with a RuntimeError.
 """
 from .api import (CooTensor, CPLoss, acc_dtype, convert, cp_als, cp_als_sweep, cp_loss,  # noqa: F401
-                  cp_loss_bwd, cp_loss_fwd, cp_loss_fwd_bwd, fiber_coords, fibers, mttkrp, tew_eq,
-                  ts, ttm, ttv, use_torch_allocator)
+                  cp_loss_bwd, cp_loss_fwd, cp_loss_fwd_bwd, fiber_coords, fibers, grid_cap, mttkrp,
+                  tew_eq, ts, ttm, ttv, use_torch_allocator)
 from ._lib import PastaError  # noqa: F401
 
 __all__ = ["CooTensor", "CPLoss", "cp_loss", "cp_loss_fwd", "cp_loss_bwd", "cp_loss_fwd_bwd", "mttkrp",
            "cp_als_sweep", "cp_als", "tew_eq", "ts", "fibers", "fiber_coords", "ttm", "ttv", "convert",
-           "acc_dtype", "use_torch_allocator", "PastaError"]
+           "acc_dtype", "use_torch_allocator", "grid_cap", "PastaError"]

@@ -57,6 +57,8 @@ SIGNATURES = {
     "pasta_ttm": (_I, [_P, _I, _P, _I, _I, _P, _P]),
     "pasta_ttv": (_I, [_P, _I, _P, _I, _P, _P]),
     "pasta_set_allocator": (_I, [_P, _P, _P]),
+    "pasta_set_grid_cap": (_I, [_I]),
+    "pasta_get_grid_cap": (_I, []),
 }
 
 _lock = threading.Lock()

@@ -490,3 +490,25 @@ class CPLoss(torch.autograd.Function):
 def cp_loss(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = BWD_PER_MODE) -> torch.Tensor:
     """Differentiable sparse CP loss (see CPLoss)."""
     return CPLoss.apply(X, mode, *Us)
+
+
+class grid_cap:
+    """Context manager limiting every MTTKRP / CP-loss launch to at most
+    ``max_blocks`` thread blocks (``pasta_set_grid_cap``; 0 = no limit), so
+    that small inputs walk the kernels' multi-round (grid-strided) path.
+    Restores the previous cap on exit.  A diagnostic: results depend on it
+    only through FP32 rounding."""
+
+    def __init__(self, max_blocks: int):
+        self.max_blocks = int(max_blocks)
+        self._prev = 0
+
+    def __enter__(self):
+        L = _lib.lib()
+        self._prev = L.pasta_get_grid_cap()
+        _lib.check(L.pasta_set_grid_cap(self.max_blocks), "pasta_set_grid_cap")
+        return self
+
+    def __exit__(self, *exc):
+        _lib.check(_lib.lib().pasta_set_grid_cap(self._prev), "pasta_set_grid_cap")
+        return False

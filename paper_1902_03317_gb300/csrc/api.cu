@@ -17,7 +17,10 @@ namespace pasta {
 namespace {
 thread_local char g_err[512] = "";
 constexpr int kPartialsCap = 4096;
+std::atomic<int> g_grid_cap{0};
 }  // namespace
+
+int grid_cap() { return g_grid_cap.load(std::memory_order_relaxed); }
 
 void set_error(const char *fmt, ...) {
     va_list ap;
@@ -777,6 +780,17 @@ pasta_status pasta_ttv(pasta_coo X, int mode, const void *d_v, pasta_dtype v_dty
                        void *stream) {
     return pasta_ttm(X, mode, d_v, v_dtype, 1, d_y, stream);
 }
+
+pasta_status pasta_set_grid_cap(int max_blocks) {
+    if (max_blocks < 0) {
+        set_error("pasta_set_grid_cap: max_blocks %d < 0", max_blocks);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    pasta::g_grid_cap.store(max_blocks, std::memory_order_relaxed);
+    return PASTA_OK;
+}
+
+int pasta_get_grid_cap(void) { return pasta::grid_cap(); }
 
 pasta_status pasta_set_allocator(pasta_alloc_fn alloc, pasta_free_fn free_fn, void *ctx) {
     if ((alloc == nullptr) != (free_fn == nullptr)) {

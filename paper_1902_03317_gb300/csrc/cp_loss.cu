@@ -357,7 +357,7 @@ int grid_for(K kernel, uint64_t nnz, const Geometry &g, int num_sms, int cap) {
     const uint64_t want = std::max<uint64_t>(1, (nwt + kThreads / 32 - 1) / (kThreads / 32));
     uint64_t b = std::min<uint64_t>(want, (uint64_t)num_sms * (uint64_t)per_sm);
     if (cap > 0) b = std::min<uint64_t>(b, (uint64_t)cap);
-    return (int)b;
+    return (int)apply_grid_cap(b);
 }
 
 template <typename T, int VEC, int J, int NM>

@@ -225,7 +225,7 @@ pasta_status run(const pasta_coo_s *X, const StoredCopy &c, const void *const *U
     const uint64_t nwt = (X->nnz + (uint64_t)g.tile * G - 1) / ((uint64_t)g.tile * G);
     const uint64_t wpb = kThreads / 32;
     const uint64_t want = (nwt + wpb - 1) / wpb;
-    const int blocks = (int)std::min<uint64_t>(want, (uint64_t)X->num_sms * (uint64_t)per_sm);
+    const int blocks = (int)apply_grid_cap(std::min<uint64_t>(want, (uint64_t)X->num_sms * (uint64_t)per_sm));
     k_mttkrp<T, VEC, J, NM><<<blocks, kThreads, 0, s>>>(a);
     PASTA_CUDA(cudaGetLastError());
     return PASTA_OK;

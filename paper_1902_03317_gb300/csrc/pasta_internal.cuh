@@ -22,6 +22,14 @@ constexpr uint64_t kPadEntries = 1024;    // stored arrays are padded to this mu
 void set_error(const char *fmt, ...);
 pasta_status cuda_fail(cudaError_t e, const char *where);
 
+// Upper bound on the thread blocks of one MTTKRP / CP-loss launch
+// (pasta_set_grid_cap; 0 = none), and `blocks` limited by it.
+int grid_cap();
+inline unsigned long long apply_grid_cap(unsigned long long blocks) {
+    const int c = grid_cap();
+    return (c > 0 && blocks > (unsigned long long)c) ? (unsigned long long)c : blocks;
+}
+
 // The library's device buffers go through these (pasta_set_allocator).
 cudaError_t dev_malloc(void **p, size_t bytes, cudaStream_t stream);
 void dev_free(void *p);

@@ -21,7 +21,8 @@
 // the warp's group tiles equal rows among its slots are summed and added
 // once.  A row spanning many tiles thus costs one atomic per warp tile (G
 // group tiles, 2048 entries at R = 32 FP32), which also keeps its FP32
-// rounding chain short.
+// rounding chain short; the add is red.global.add.v4.f32, four columns per
+// lane.
 //
 // L2 policy: factor rows are re-read across the whole launch (evict-last).
 #pragma once
@@ -398,12 +399,19 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
                     if (ru != row) break;
                     end = u;
                 }
-                for (int t = lane; t < (int)a.R; t += 32) {
-                    float sum = 0.f;
+                // R is a multiple of 4 (R * sizeof(T) = 16 L) and the slot rows
+                // and the output are 16-byte aligned: one vector add per 4 columns.
+                for (int t = 4 * lane; t < (int)a.R; t += 128) {
+                    float sum[4] = {0.f, 0.f, 0.f, 0.f};
                     for (int u = h; u <= end; ++u)
-                        if (*slot_row(u) == row) sum += slot_val(u)[t];
-                    asm volatile("red.global.add.f32 [%0], %1;" ::"l"(a.out + (uint64_t)row * a.R + t),
-                                 "f"(sum));
+                        if (*slot_row(u) == row) {
+                            const float4 v = *reinterpret_cast<const float4 *>(slot_val(u) + t);
+                            sum[0] += v.x;
+                            sum[1] += v.y;
+                            sum[2] += v.z;
+                            sum[3] += v.w;
+                        }
+                    RedAdd<float, 4>::run(a.out + (uint64_t)row * a.R + t, sum);
                 }
             }
             __syncwarp();  // the slots are staging words again in the next tile

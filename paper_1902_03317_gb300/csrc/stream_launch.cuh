@@ -95,6 +95,7 @@ pasta_status run(const StreamLaunch &l, cudaStream_t s) {
     const uint64_t nbt0 = std::max<uint64_t>(1, (l.nnz + longest * per_bt - 1) / (longest * per_bt));
     uint64_t blocks = std::min<uint64_t>(nbt0, (uint64_t)l.num_sms * (uint64_t)per_sm);
     if (l.max_blocks > 0) blocks = std::min<uint64_t>(blocks, (uint64_t)l.max_blocks);
+    blocks = apply_grid_cap(blocks);
     const uint64_t rounds = (nbt0 + blocks - 1) / blocks;
     const uint64_t need = (l.nnz + blocks * rounds * per_bt - 1) / (blocks * rounds * per_bt);
     a.tile = (int)std::min<uint64_t>(longest, std::max<uint64_t>(chunk, (need + chunk - 1) / chunk * chunk));

@@ -4,8 +4,11 @@ This entry point serves callers that must not allocate device memory where
 they compute the loss (inside another framework's stream capture, in
 real-time or callback code, or next to a foreign allocator): it reads the
 caller's own arrays and keeps its scratch in a fixed device array inside the
-library.  Its results must match pasta_cp_loss_fwd on the same entries, on
-two calls in a row (the second call reuses the scratch the first one left).
+library.  Its results must match pasta_cp_loss_fwd on the same entries and
+the FP64 oracle, on two calls in a row (the second call reuses the scratch
+the first one left).  The cases cover the streaming kernel (FP32 R = 32,
+BF16 R = 16 order 5) and the general kernel (FP32 R = 24, whose row is not a
+power-of-two number of 16-byte slots, and FP64 factors).
 """
 import ctypes
 
@@ -13,6 +16,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 import paper_1902_03317_gb300 as pasta
 from paper_1902_03317_gb300 import _lib, synth
 from tests import _gpu as G
@@ -31,14 +35,20 @@ def _padded(t: torch.Tensor) -> torch.Tensor:
 @pytest.mark.parametrize("name,nnz,dims,R,dtype", [
     ("zipf3d", 200_001, (20_000, 10_000, 4_000), 32, torch.float32),
     ("zipf5d", 100_003, (8, 50_000, 10_000, 1_000, 100), 16, torch.bfloat16),
+    ("zipf3d", 60_001, (5_000, 3_000, 1_000), 24, torch.float32),
+    ("zipf4d", 30_002, (900, 800, 70, 20), 8, torch.float64),
 ])
 def test_noalloc_loss_matches_handle_path(name, nnz, dims, R, dtype):
     Xh = synth.generate(G.small(name, nnz, dims))
     X = G.to_device(Xh)
-    _, Us, _ = G.factors(dims, R, 21, dtype)
+    _, Us, rounded = G.factors(dims, R, 21, dtype)
     ref_loss, ref_e = pasta.cp_loss_fwd(X, Us, -1, want_resid=True)
     ref_loss = ref_loss.item()
     ref_e = ref_e.cpu().numpy()
+    idx_h, val_h = G.host(Xh)
+    o_loss, o_e = oracle.cp_loss(dims, idx_h, val_h, rounded, want_resid=True)
+    tol = 1e-12 if dtype == torch.float64 else G.FP32_TOL
+    rdt = torch.float64 if dtype == torch.float64 else torch.float32
 
     idx = [_padded(i.to(G.DEV)) for i in Xh.idx]
     val = _padded(Xh.val.to(G.DEV))
@@ -46,15 +56,17 @@ def test_noalloc_loss_matches_handle_path(name, nnz, dims, R, dtype):
     stream = torch.cuda.current_stream().cuda_stream
     for call in range(2):
         loss = torch.full((), float("nan"), dtype=torch.float64, device=G.DEV)
-        e = torch.full((nnz,), float("nan"), dtype=torch.float32, device=G.DEV)
+        e = torch.full((nnz,), float("nan"), dtype=rdt, device=G.DEV)
         st = lib.pasta_cp_loss_fwd_noalloc(
             len(dims), _lib.u64_array(dims), nnz, _lib.ptr_array([t.data_ptr() for t in idx]),
             val.data_ptr(), _lib.ptr_array([u.data_ptr() for u in Us]), pasta.api.pasta_dtype(dtype),
             R, loss.data_ptr(), e.data_ptr(), stream)
         _lib.check(st, "pasta_cp_loss_fwd_noalloc")
         torch.cuda.synchronize()
-        assert abs(loss.item() - ref_loss) <= G.FP32_TOL * ref_loss, call
-        assert G.rel_err(e.cpu().numpy(), ref_e) < G.FP32_TOL, call
+        assert abs(loss.item() - ref_loss) <= tol * ref_loss, call
+        assert G.rel_err(e.cpu().numpy(), ref_e) < tol, call
+        assert abs(loss.item() - o_loss) <= tol * o_loss, call
+        assert G.rel_err(e.cpu().numpy(), o_e) < tol, call
     X.close()
 
 
