@@ -58,6 +58,11 @@ def parse():
                          "(small cases for profiling; not a bench line)")
     ap.add_argument("--cpu-sample", type=int, default=12_000_000,
                     help="entries of the workload the CPU oracle runs on")
+    ap.add_argument("--no-legs", action="store_true",
+                    help="skip the extra measured legs (gather ceiling, L2-flushed MTTKRP, BF16 factors, "
+                         "zipf4d and zipf5d)")
+    ap.add_argument("--no-multicore", action="store_true",
+                    help="skip the multicore CPU baseline (privatized OpenMP MTTKRP)")
     return ap.parse_args()
 
 
@@ -319,6 +324,11 @@ def run_own(args, rank, world, local):
     del Xd
     torch.cuda.empty_cache()
 
+    if not args.no_legs and rank == 0:
+        result["gather_ceiling"] = gather_ceiling(pasta, X, Us, wl, per_mode_ms, peak, args)
+        result["l2_flush"] = l2_flush_leg(pasta, X, Us, wl, per_mode_ms, args)
+        if args.factor_dtype == "f32":
+            result["bf16_factors"] = bf16_leg(pasta, X, wl, touched, peak, args, dev)
     if not args.no_ttm and rank == 0:
         result["ttm_ttv"] = ttm_timing(pasta, X, wl, peak, args)
     if not args.no_tew and rank == 0:
@@ -330,13 +340,166 @@ def run_own(args, rank, world, local):
     if not args.no_e2e:
         result["e2e"] = e2e(pasta, synth, wl, dev, args, world)
     if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(wl, args)
+        result["cpu_baseline"] = cpu_baseline(wl, args, pasta, dev)
     X.close()
+    del Us, Ms
+    torch.cuda.empty_cache()
+    if rank == 0 and not args.no_multicore and not args.no_cpu_baseline and not args.nnz:
+        result["cpu_multicore"] = cpu_multicore(wl, args)
+    if not args.no_legs and rank == 0 and not args.nnz:
+        result["workloads"] = {name: workload_leg(pasta, synth, name, dts, peak, args, dev, loss)
+                               for name, dts, loss in (("zipf4d", ("f32", "bf16"), False),
+                                                       ("zipf5d", ("bf16",), True))}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def _time_ms(fn, reps):
+    """Mean device time of fn() over reps calls (CUDA events on the current stream)."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def mttkrp_alg_bytes(nnz, N, R, es, touched, dims, n):
+    """Compulsory bytes of one mode-n MTTKRP: the COO stream (N 32-bit
+    indices + FP32 value per entry), every touched row of the other factors
+    (element size es) once, the FP32 output once."""
+    return nnz * (4 * N + 4) + sum(touched[k] * R * es for k in range(N) if k != n) + dims[n] * R * 4
+
+
+def gather_ceiling(pasta, X, Us, wl, mttkrp_ms, peak, args):
+    """pasta_gather_probe per mode: the same kernel, launch and row gathers as
+    the MTTKRP with no arithmetic into output rows.  Its time is the ceiling
+    the MTTKRP kernel can reach with these gathers; also reported as the
+    gathered bytes per second through L1/L2 (every entry's N-1 rows of R
+    elements, hits included)."""
+    import torch
+    N = wl.order
+    sink = torch.empty(1 << 22, dtype=torch.float32, device=X.device)
+    K = max(5, args.steps // 2)
+    es = Us[0].element_size()
+    out = {"what": "pasta_gather_probe: MTTKRP's staging, batches and row gathers, no arithmetic or output rows",
+           "ms_per_mode": [], "gathered_bytes_per_mode": wl.nnz * (N - 1) * wl.R * es,
+           "gathered_gbs": [], "mttkrp_ms_per_mode": [round(x, 4) for x in mttkrp_ms],
+           "mttkrp_over_probe": []}
+    for n in range(N):
+        ms = _time_ms(lambda: pasta.gather_probe(X, Us, n, sink=sink), K)
+        out["ms_per_mode"].append(round(ms, 4))
+        out["gathered_gbs"].append(round(out["gathered_bytes_per_mode"] / (ms * 1e-3) / 1e9, 1))
+        out["mttkrp_over_probe"].append(round(mttkrp_ms[n] / ms, 3))
+    return out
+
+
+def l2_flush_leg(pasta, X, Us, wl, mttkrp_ms, args):
+    """MTTKRP per mode with L2 flushed before every call (a 512 MB buffer
+    written between calls, outside the timed events), against the unflushed
+    back-to-back calls of the timed step: what carrying factor rows in L2
+    from one call to the next (evict-last policy) is worth."""
+    import torch
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=X.device)
+    K = max(5, args.steps // 2)
+    Ms = [torch.empty((wl.dims[n], wl.R), device=X.device) for n in range(wl.order)]
+    flushed = []
+    for n in range(wl.order):
+        tot = 0.0
+        for _ in range(K):
+            flush.fill_(1)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            pasta.mttkrp(X, Us, n, out=Ms[n])
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        flushed.append(round(tot / K, 4))
+    return {"flush": "512 MB written before each call (L2 is 126 MB)", "flushed_ms_per_mode": flushed,
+            "unflushed_ms_per_mode": [round(x, 4) for x in mttkrp_ms],
+            "flushed_over_unflushed": [round(f / u, 3) for f, u in zip(flushed, mttkrp_ms)]}
+
+
+def bf16_leg(pasta, X, wl, touched, peak, args, dev):
+    """The benchmark tensor with BF16 factors (FP32 accumulation): MTTKRP per
+    mode and the fused loss + gradients, with the compulsory-byte rooflines."""
+    import torch
+    from paper_1902_03317_gb300 import synth
+    N = wl.order
+    Ub = [u.to(torch.bfloat16).contiguous() for u in synth.factors_for(wl, device=dev)]
+    K = max(5, args.steps // 2)
+    ms = [_time_ms(lambda: pasta.mttkrp(X, Ub, n), K) for n in range(N)]
+    loss_ms = _time_ms(lambda: pasta.cp_loss_fwd_bwd(X, Ub), K)
+    alg = [mttkrp_alg_bytes(wl.nnz, N, wl.R, 2, touched, wl.dims, n) for n in range(N)]
+    gbs = sum(alg) / (sum(ms) * 1e-3) / 1e9
+    lalg = [wl.nnz * (4 * N + 4) + sum(touched[k] * wl.R * 2 for k in range(N)) + wl.dims[n] * wl.R * 4
+            for n in range(N)]
+    lgbs = sum(lalg) / (loss_ms * 1e-3) / 1e9
+    return {"mttkrp_ms_per_mode": [round(x, 4) for x in ms], "value_nnz_per_s": N * wl.nnz / (sum(ms) * 1e-3),
+            "mttkrp_alg_bytes_per_mode": alg, "mttkrp_achieved_gbs": round(gbs, 1),
+            "mttkrp_frac": round(gbs / peak, 4), "loss_fwd_bwd_ms": round(loss_ms, 4),
+            "loss_achieved_gbs": round(lgbs, 1), "loss_frac": round(lgbs / peak, 4)}
+
+
+def workload_leg(pasta, synth, name, dts, peak, args, dev, with_loss):
+    """Another configuration at its full size: generate, sort every mode,
+    then MTTKRP per mode (and, with_loss, the fused loss + gradients) for each
+    factor type, with compulsory-byte rooflines.  Parity of these shapes
+    against the oracle is covered by the test suite (full-size sampled-row
+    checks, scaled element-wise checks)."""
+    import torch
+    wl = synth.WORKLOADS[name]
+    N = wl.order
+    Xd = synth.generate(wl, device=dev)
+    touched = [int(torch.unique(ix).numel()) for ix in Xd.idx]
+    X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
+    del Xd
+    torch.cuda.empty_cache()
+    t_sort = []
+    for n in range(N):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        X.sort_by_mode(n)
+        b.record()
+        torch.cuda.synchronize()
+        t_sort.append(round(a.elapsed_time(b), 3))
+    out = {"workload": workload_desc(wl), "sort_ms_per_mode": t_sort}
+    K = max(5, args.steps // 3)
+    for dt in dts:
+        tdt = {"f32": torch.float32, "bf16": torch.bfloat16}[dt]
+        es = 4 if dt == "f32" else 2
+        Us = [u.to(tdt).contiguous() for u in synth.factors_for(wl, device=dev)]
+        Ms = [torch.empty((wl.dims[n], wl.R), device=dev) for n in range(N)]
+        ms = [_time_ms(lambda: pasta.mttkrp(X, Us, n, out=Ms[n]), K) for n in range(N)]
+        alg = [mttkrp_alg_bytes(wl.nnz, N, wl.R, es, touched, wl.dims, n) for n in range(N)]
+        gbs = sum(alg) / (sum(ms) * 1e-3) / 1e9
+        leg = {"mttkrp_ms_per_mode": [round(x, 4) for x in ms],
+               "value_nnz_per_s": N * wl.nnz / (sum(ms) * 1e-3),
+               "mttkrp_alg_bytes_per_mode": alg, "mttkrp_achieved_gbs": round(gbs, 1),
+               "mttkrp_frac": round(gbs / peak, 4)}
+        if with_loss:
+            lms = _time_ms(lambda: pasta.cp_loss_fwd_bwd(X, Us), K)
+            lalg = sum(wl.nnz * (4 * N + 4) + sum(touched[k] * wl.R * es for k in range(N)) + wl.dims[n] * wl.R * 4
+                       for n in range(N))
+            leg["loss_fwd_bwd_ms"] = round(lms, 4)
+            leg["loss_achieved_gbs"] = round(lalg / (lms * 1e-3) / 1e9, 1)
+            leg["loss_frac"] = round(lalg / (lms * 1e-3) / 1e9 / peak, 4)
+        out[dt] = leg
+        del Us, Ms
+    X.close()
+    torch.cuda.empty_cache()
+    return out
 
 
 def sort_roofline(t_sort, nnz, N, peak):
@@ -604,16 +767,59 @@ def oracle_sample(wl, sample: int):
     return idx, val, U, n
 
 
-def cpu_baseline(wl, args):
+def cpu_baseline(wl, args, pasta=None, dev=None):
+    """The FP64 oracle, one thread, on a bounded sample of the workload (all
+    modes).  The same sample also runs through the library on the GPU, and
+    the relative Frobenius error of each mode's output against the oracle's
+    is reported."""
+    import numpy as np
     import oracle
     idx, val, U, n = oracle_sample(wl, args.cpu_sample)
     t0 = time.perf_counter()
-    for mode in range(wl.order):
-        oracle.mttkrp(wl.dims, idx, val, U, mode, wl.R)
+    refs = [oracle.mttkrp(wl.dims, idx, val, U, mode, wl.R) for mode in range(wl.order)]
     dt = time.perf_counter() - t0
-    return {"value": wl.order * n / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {n:,} of {wl.nnz:,} entries (random storage order), MTTKRP on all "
-                      f"{wl.order} modes, FP64 C oracle, 1 thread: {dt:.1f} s"}
+    out = {"value": wl.order * n / dt, "unit": "nnz/s", "cores": 1, "kind": "oracle",
+           "sample": f"first {n:,} of {wl.nnz:,} entries (random storage order), MTTKRP on all "
+                     f"{wl.order} modes, FP64 C oracle, 1 thread: {dt:.1f} s"}
+    if pasta is not None:
+        import torch
+        Xs = pasta.CooTensor(wl.dims, [torch.from_numpy(i.astype(np.int32)).to(dev) for i in idx],
+                             torch.from_numpy(val.astype(np.float32)).to(dev))
+        Ug = [torch.from_numpy(u.astype(np.float32)).to(dev) for u in U]
+        errs = []
+        for mode in range(wl.order):
+            M = pasta.mttkrp(Xs, Ug, mode).double().cpu().numpy()
+            errs.append(float(np.linalg.norm(M - refs[mode]) / np.linalg.norm(refs[mode])))
+        Xs.close()
+        out["gpu_rel_err_vs_oracle"] = errs
+    return out
+
+
+def cpu_multicore(wl, args):
+    """The paper's multicore MTTKRP (Sec. 5.3: parallel loop over the stored
+    entries, privatized outputs, then a parallel reduction), FP32, on every
+    host core, over the whole workload, all modes.  A baseline only."""
+    import numpy as np
+    import oracle
+    from paper_1902_03317_gb300 import synth
+    import torch
+    Xd = synth.generate(wl, device="cuda" if torch.cuda.is_available() else "cpu")
+    idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
+    val = Xd.val.cpu().numpy()
+    del Xd
+    U = [u.numpy() for u in synth.factors_for(wl)]
+    threads = oracle.cpu_threads()
+    oracle.mttkrp_privatized(wl.dims, [i[:100_000] for i in idx], val[:100_000], U, 0)  # warm-up
+    times = []
+    for mode in range(wl.order):
+        t0 = time.perf_counter()
+        oracle.mttkrp_privatized(wl.dims, idx, val, U, mode)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times)
+    return {"value": wl.order * wl.nnz / dt, "unit": "nnz/s", "cores": threads,
+            "kind": "privatized OpenMP MTTKRP, FP32 (the paper's Sec. 5.3 scheme)",
+            "s_per_mode": [round(t, 3) for t in times], "nproc": os.cpu_count(),
+            "sample": f"whole workload ({wl.nnz:,} entries), all {wl.order} modes"}
 
 
 def run_reference(args, rank, world):

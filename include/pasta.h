@@ -179,6 +179,25 @@ pasta_status pasta_mttkrp(pasta_coo X, const void *const *d_U, pasta_dtype u_dty
                           int R, void *d_M, void *stream);
 
 /*
+ * pasta_gather_probe -- diagnostic companion of pasta_mttkrp (not a paper
+ * operation).  Streams the mode-`mode` sorted copy with the same kernel,
+ * geometry and launch as pasta_mttkrp and gathers, for every stored entry,
+ * the same N-1 factor rows, but neither multiplies them by the value nor
+ * reduces them into output rows: each thread sums what it gathered and
+ * writes that one float to d_sink.  Its time is the row-gather ceiling of
+ * pasta_mttkrp on that tensor (the cost of the gathers alone, at the
+ * kernel's own parallelism).
+ *   d_U, u_dtype, mode, R  as for pasta_mttkrp
+ *   d_sink     device buffer of sink_len floats (>= 256); the launch uses at
+ *              most sink_len / 256 thread blocks; contents are meaningless
+ * PASTA_ERR_UNSUPPORTED outside the streaming MTTKRP's cases (FP32/BF16/FP16
+ * factors, order 2..5, R * sizeof(element) = 16 L with L a power of two,
+ * 16-byte aligned factors and sink).  Asynchronous on `stream`.
+ */
+pasta_status pasta_gather_probe(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int mode,
+                                int R, float *d_sink, uint64_t sink_len, void *stream);
+
+/*
  * pasta_cp_loss_fwd -- sparse CP least-squares loss over the stored entries:
  *     model(m) = sum_r prod_k U_k(i_k(m), r),   e(m) = val(m) - model(m),
  *     loss = 1/2 * sum_m e(m)^2.
@@ -417,6 +436,84 @@ pasta_status pasta_ttm(pasta_coo X, int mode, const void *d_U, pasta_dtype u_dty
  * elements, d_y nfibs). */
 pasta_status pasta_ttv(pasta_coo X, int mode, const void *d_v, pasta_dtype v_dtype, void *d_y,
                        void *stream);
+
+/*
+ * Range forms, for splitting one tensor over several processes or devices
+ * (each computing a contiguous range of the stored entries, the partial
+ * results then summed, e.g. by an all-reduce: Sec. 5.3's privatization, the
+ * partial outputs being the ranks' instead of the threads').  Not paper
+ * operations.
+ *
+ * pasta_mttkrp_range -- pasta_mttkrp restricted to the entries at positions
+ * [lo, hi) of the mode-`mode` sorted copy: d_M (dims[mode] x R) is
+ * overwritten with their MTTKRP (rows they do not reach are 0).  Summing the
+ * outputs of ranges that partition [0, nnz) gives pasta_mttkrp's result (to
+ * FP32 rounding).  lo must be a multiple of 4 (PASTA_ERR_ALIGNMENT) and
+ * lo <= hi <= nnz (PASTA_ERR_INVALID_ARG).
+ */
+pasta_status pasta_mttkrp_range(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int mode, int R,
+                                uint64_t lo, uint64_t hi, void *d_M, void *stream);
+
+/*
+ * pasta_cp_loss_fwd_bwd_range -- pasta_cp_loss_fwd_bwd over the entries at
+ * positions [lo, hi) of every sorted copy: pass k covers [lo, hi) of the
+ * mode-k copy, and the loss is summed over [lo, hi) of the mode-0 copy.
+ * Ranges that partition [0, nnz) therefore cover every entry once in each
+ * pass, and the sums of their losses and gradients are the whole tensor's.
+ * Same arguments as pasta_cp_loss_fwd_bwd plus lo, hi (limits as for
+ * pasta_mttkrp_range).
+ */
+pasta_status pasta_cp_loss_fwd_bwd_range(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int R,
+                                         uint64_t lo, uint64_t hi, double *d_loss, const double *d_gscale,
+                                         void *const *d_G, void *stream);
+
+/*
+ * pasta_coo_hicoo -- build (once per block size) the HiCOO copy of X: the
+ * hierarchical COO format (Li, Choi and Vuduc, SC'18) that Sec. 8 names with
+ * CSF as the compressed formats to add.  The index space is cut into blocks
+ * of 2^block_bits cells per mode; entry coordinate i_k splits into the block
+ * coordinate i_k >> block_bits and the offset i_k & (2^block_bits - 1).  The
+ * copy holds the nonempty blocks (bptr: nb + 1 entry positions, the last one
+ * nnz; binds[k]: nb block coordinates per mode, uint32) and, per entry in
+ * block order, one offset byte per mode (einds[k]) and the FP32 value.
+ * Blocks are in lexicographic order of their coordinates (mode 0 first);
+ * entries of a block in lexicographic order of their offsets.  Both come
+ * from one stable sort of the key (block coordinates, each mode taking
+ * ceil(log2(ceil(dims[k] / 2^block_bits))) bits, then the offsets,
+ * block_bits each), cut to its leading 64 bits; where offset bits are cut,
+ * entries with equal leading bits keep creation order.  One copy serves
+ * every mode.
+ *   block_bits  1..8 (PASTA_ERR_INVALID_ARG otherwise); a later call with
+ *               another value rebuilds the copy
+ *   nblocks     host output (may be NULL): nb
+ * PASTA_ERR_UNSUPPORTED when the block coordinates need more than 64 key
+ * bits.  Synchronises `stream` (block count, then the end of the build).
+ * Device memory: N + 4 bytes per entry (padded like the stored copies) plus
+ * 4 N + 4 per block, freed by pasta_coo_destroy; the sort uses the handle's
+ * scratch.
+ */
+pasta_status pasta_coo_hicoo(pasta_coo X, int block_bits, uint64_t *nblocks, void *stream);
+
+/* Copy the HiCOO arrays into caller-owned device buffers (any may be NULL;
+ * d_binds / d_einds are host arrays of N device pointers, entries may be
+ * NULL): d_bptr nb + 1 uint32, d_binds[k] nb uint32, d_einds[k] nnz bytes,
+ * d_val nnz FP32.  PASTA_ERR_NOT_SORTED without a HiCOO copy.  Asynchronous. */
+pasta_status pasta_hicoo_copy_out(pasta_coo X, uint32_t *d_bptr, uint32_t *const *d_binds,
+                                  uint8_t *const *d_einds, float *d_val, void *stream);
+
+/*
+ * pasta_hicoo_mttkrp -- the mode-n MTTKRP of pasta_mttkrp (Eq.
+ * (mttkrp-init)), computed from the HiCOO copy (PASTA_ERR_NOT_SORTED if
+ * absent) instead of a mode-sorted copy.  Same arguments and output.  The
+ * copy is not ordered by the output mode, so rows are summed in two
+ * register slots per lane group and added with vector atomics when evicted;
+ * the summation order, and so the FP32 rounding, differs from pasta_mttkrp.
+ * Covers FP32/BF16/FP16 factors, order 2..5, R * sizeof(element) = 16 L with
+ * L a power of two, 16-byte aligned factors and output; otherwise
+ * PASTA_ERR_UNSUPPORTED.
+ */
+pasta_status pasta_hicoo_mttkrp(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int mode, int R,
+                                void *d_M, void *stream);
 
 /*
  * pasta_set_grid_cap -- upper bound on the thread blocks of every MTTKRP and

@@ -38,8 +38,10 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile ``pasta_oracle.c`` into ``oracle/_build/liboracle.so``."""
+    """Compile ``pasta_oracle.c`` into ``oracle/_build/liboracle.so`` (and the
+    multicore CPU baseline, see ``build_parallel``)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    build_parallel(force)
     if (not force and os.path.exists(_LIB)
             and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
         return _LIB
@@ -49,6 +51,68 @@ def build(force: bool = False) -> str:
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB)
     return _LIB
+
+
+_PAR_SRC = os.path.join(_HERE, "pasta_cpu_parallel.c")
+_PAR_LIB = os.path.join(_HERE, "_build", "libcpu_parallel.so")
+_par = None
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile the multicore CPU baseline ``pasta_cpu_parallel.c`` (the
+    privatization MTTKRP of Sec. 5.3, FP32, OpenMP; a timed baseline, not a
+    correctness reference) into ``oracle/_build/libcpu_parallel.so``."""
+    os.makedirs(os.path.dirname(_PAR_LIB), exist_ok=True)
+    if (not force and os.path.exists(_PAR_LIB)
+            and os.path.getmtime(_PAR_LIB) >= os.path.getmtime(_PAR_SRC)):
+        return _PAR_LIB
+    tmp = _PAR_LIB + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O3", "-fopenmp", "-std=c11", "-shared", "-fPIC", "-o", tmp, _PAR_SRC]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _PAR_LIB)
+    return _PAR_LIB
+
+
+def _load_parallel():
+    global _par
+    with _lock:
+        if _par is None:
+            lib = ctypes.CDLL(build_parallel())
+            P = ctypes.c_void_p
+            lib.cpu_mttkrp_privatized.argtypes = [ctypes.c_int, P, ctypes.c_uint64, P, P, P,
+                                                  ctypes.c_int, ctypes.c_int, P, ctypes.c_int]
+            lib.cpu_mttkrp_privatized.restype = ctypes.c_int
+            lib.cpu_threads.argtypes = []
+            lib.cpu_threads.restype = ctypes.c_int
+            _par = lib
+    return _par
+
+
+def cpu_threads() -> int:
+    """Threads the multicore baseline uses by default (OpenMP's count)."""
+    return int(_load_parallel().cpu_threads())
+
+
+def mttkrp_privatized(dims, idx, val, U, mode: int, threads: int = 0) -> np.ndarray:
+    """Mode-``mode`` MTTKRP in FP32 on ``threads`` host threads (0 = all),
+    each accumulating a private copy of the output that a parallel pass then
+    sums (Sec. 5.3's privatization).  Inputs are converted to FP32 / uint32;
+    ``U[mode]`` may be None.  Returns the ``dims[mode] x R`` FP32 output."""
+    dims = np.ascontiguousarray(np.asarray(dims, dtype=np.uint64))
+    order = int(dims.shape[0])
+    idx = [np.ascontiguousarray(np.asarray(ix).astype(np.uint32, copy=False)) for ix in idx]
+    val = np.ascontiguousarray(np.asarray(val, dtype=np.float32))
+    R = next(np.asarray(u).shape[1] for k, u in enumerate(U) if u is not None and k != mode)
+    Uf = [np.zeros((1, R), np.float32) if (u is None or k == mode)
+          else np.ascontiguousarray(np.asarray(u, dtype=np.float32)) for k, u in enumerate(U)]
+    M = np.empty((int(dims[mode]), R), dtype=np.float32)
+    ip = (ctypes.c_void_p * order)(*[_ptr(ix) for ix in idx])
+    up = (ctypes.c_void_p * order)(*[_ptr(u) for u in Uf])
+    rc = _load_parallel().cpu_mttkrp_privatized(order, _ptr(dims), int(val.shape[0]), ip, _ptr(val), up,
+                                                int(mode), int(R), _ptr(M), int(threads))
+    if rc != 0:
+        raise ValueError("cpu_mttkrp_privatized rejected its arguments or ran out of memory")
+    return M
 
 
 def _load():
@@ -315,3 +379,46 @@ def ttv(dims, idx, val, v, mode: int):
     (fiber_coords, y with one value per fiber)."""
     coords, Y = ttm(dims, idx, val, np.asarray(v, dtype=np.float64)[:, None], mode)
     return coords, Y[:, 0]
+
+
+def hicoo(dims, idx, val, bits: int):
+    """The HiCOO copy (Li, Choi and Vuduc, SC'18; Sec. 8 names it as a format
+    to add) from its definition: blocks of 2^bits cells per mode; an entry's
+    block coordinate is i_k >> bits, its offset i_k & (2^bits - 1).  Entries
+    are ordered by one stable sort of the key made of the block coordinates
+    (mode 0 most significant, each mode ceil(log2(number of blocks)) bits)
+    followed by the offsets (mode 0 first, bits each), cut to its leading 64
+    bits (numpy's stable argsort as the sorting step).  Returns
+    (bptr [nb + 1], binds: N arrays [nb], einds: N arrays [nnz] (uint8),
+    val [nnz], perm [nnz]: creation-order entry of each position)."""
+    dims = [int(d) for d in dims]
+    N = len(dims)
+    idx = [np.asarray(i, dtype=np.uint64) for i in idx]
+    nnz = int(idx[0].shape[0]) if N else 0
+    bb = []
+    for d in dims:
+        nblk = (d + (1 << bits) - 1) >> bits
+        bb.append(int(nblk - 1).bit_length())
+    BB = sum(bb)
+    if BB > 64:
+        raise ValueError("block coordinates need more than 64 key bits")
+    E = min(64 - BB, N * bits)
+    block_key = np.zeros(nnz, dtype=np.uint64)
+    elem_key = np.zeros(nnz, dtype=np.uint64)
+    mask = np.uint64((1 << bits) - 1)
+    for k in range(N):
+        block_key = (block_key << np.uint64(bb[k])) | (idx[k] >> np.uint64(bits))
+        elem_key = (elem_key << np.uint64(bits)) | (idx[k] & mask)
+    drop = N * bits - E
+    e_part = elem_key >> np.uint64(drop) if drop < 64 else np.zeros(nnz, dtype=np.uint64)
+    key = (block_key << np.uint64(E)) | e_part if E < 64 else e_part
+    perm = np.argsort(key, kind="stable")
+    bk = block_key[perm]
+    heads = np.ones(nnz, dtype=bool)
+    if nnz:
+        heads[1:] = bk[1:] != bk[:-1]
+    starts = np.flatnonzero(heads)
+    bptr = np.concatenate([starts, [nnz]]).astype(np.int64)
+    binds = [(idx[k][perm][starts] >> np.uint64(bits)).astype(np.int64) for k in range(N)]
+    einds = [(idx[k][perm] & mask).astype(np.uint8) for k in range(N)]
+    return bptr, binds, einds, np.asarray(val)[perm], perm

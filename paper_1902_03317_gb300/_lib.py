@@ -58,6 +58,12 @@ SIGNATURES = {
     "pasta_ttv": (_I, [_P, _I, _P, _I, _P, _P]),
     "pasta_set_allocator": (_I, [_P, _P, _P]),
     "pasta_set_grid_cap": (_I, [_I]),
+    "pasta_gather_probe": (_I, [_P, _P, _I, _I, _I, _P, _U64, _P]),
+    "pasta_coo_hicoo": (_I, [_P, _I, _P, _P]),
+    "pasta_mttkrp_range": (_I, [_P, _P, _I, _I, _I, _U64, _U64, _P, _P]),
+    "pasta_cp_loss_fwd_bwd_range": (_I, [_P, _P, _I, _I, _U64, _U64, _P, _P, _P, _P]),
+    "pasta_hicoo_copy_out": (_I, [_P, _P, _P, _P, _P, _P]),
+    "pasta_hicoo_mttkrp": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "pasta_get_grid_cap": (_I, []),
 }
 

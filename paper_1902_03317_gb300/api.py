@@ -307,6 +307,102 @@ def mttkrp(X: CooTensor, Us: Sequence[torch.Tensor | None], mode: int,
     return out
 
 
+def mttkrp_range(X: CooTensor, Us: Sequence[torch.Tensor | None], mode: int, lo: int, hi: int,
+                 out: torch.Tensor | None = None) -> torch.Tensor:
+    """MTTKRP over the entries at positions [lo, hi) of the mode-``mode``
+    sorted copy (pasta_mttkrp_range; lo a multiple of 4).  Outputs of ranges
+    that partition the copy sum to ``mttkrp``'s."""
+    X.sort_by_mode(mode)
+    ptrs, dt, R = _factor_ptrs(X, Us, skip=mode)
+    if out is None:
+        out = torch.empty((X.dims[mode], R), dtype=acc_dtype(dt), device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_mttkrp_range(X.handle, ptrs, pasta_dtype(dt), int(mode), R, int(lo), int(hi),
+                                           out.data_ptr(), _stream(X.device))
+    _lib.check(st, "pasta_mttkrp_range")
+    return out
+
+
+def cp_loss_fwd_bwd_range(X: CooTensor, Us: Sequence[torch.Tensor], lo: int, hi: int,
+                          gscale: torch.Tensor | None = None):
+    """Loss and gradients over positions [lo, hi) of every sorted copy
+    (pasta_cp_loss_fwd_bwd_range); sums over ranges that partition the
+    entries give ``cp_loss_fwd_bwd``'s results."""
+    X.sort_all()
+    ptrs, dt, R = _factor_ptrs(X, Us)
+    loss = torch.empty((), dtype=torch.float64, device=X.device)
+    G = [torch.empty((d, R), dtype=acc_dtype(dt), device=X.device) for d in X.dims]
+    gp = None
+    if gscale is not None:
+        gscale = gscale.to(device=X.device, dtype=torch.float64).reshape(()).contiguous()
+        gp = gscale.data_ptr()
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_cp_loss_fwd_bwd_range(X.handle, ptrs, pasta_dtype(dt), R, int(lo), int(hi),
+                                                    loss.data_ptr(), gp,
+                                                    _lib.ptr_array([g.data_ptr() for g in G]), _stream(X.device))
+    _lib.check(st, "pasta_cp_loss_fwd_bwd_range")
+    return loss, G
+
+
+def hicoo(X: CooTensor, block_bits: int = 7) -> int:
+    """Build the HiCOO copy of ``X`` (pasta_coo_hicoo: blocks of
+    2^block_bits cells per mode, one offset byte per mode per entry; one copy
+    for every mode).  Returns the number of nonempty blocks."""
+    nb = ctypes.c_uint64()
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_coo_hicoo(X.handle, int(block_bits), ctypes.byref(nb), _stream(X.device))
+    _lib.check(st, "pasta_coo_hicoo")
+    return int(nb.value)
+
+
+def hicoo_copy_out(X: CooTensor, nblocks: int):
+    """The HiCOO arrays as device tensors: (bptr[nb + 1] int32, binds: list of
+    N int32 [nb], einds: list of N uint8 [nnz], val float32 [nnz])."""
+    dev = X.device
+    bptr = torch.empty(nblocks + 1, dtype=torch.int32, device=dev)
+    binds = [torch.empty(nblocks, dtype=torch.int32, device=dev) for _ in X.dims]
+    einds = [torch.empty(X.nnz, dtype=torch.uint8, device=dev) for _ in X.dims]
+    val = torch.empty(X.nnz, dtype=torch.float32, device=dev)
+    with torch.cuda.device(dev):
+        st = _lib.lib().pasta_hicoo_copy_out(X.handle, bptr.data_ptr(),
+                                             _lib.ptr_array([b.data_ptr() for b in binds]),
+                                             _lib.ptr_array([e.data_ptr() for e in einds]),
+                                             val.data_ptr(), _stream(dev))
+    _lib.check(st, "pasta_hicoo_copy_out")
+    return bptr, binds, einds, val
+
+
+def hicoo_mttkrp(X: CooTensor, Us: Sequence[torch.Tensor | None], mode: int,
+                 out: torch.Tensor | None = None) -> torch.Tensor:
+    """Mode-``mode`` MTTKRP from the HiCOO copy (built first with ``hicoo``).
+    Same result as ``mttkrp`` up to FP32 rounding."""
+    ptrs, dt, R = _factor_ptrs(X, Us, skip=mode)
+    if out is None:
+        out = torch.empty((X.dims[mode], R), dtype=acc_dtype(dt), device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_hicoo_mttkrp(X.handle, ptrs, pasta_dtype(dt), int(mode), R, out.data_ptr(),
+                                           _stream(X.device))
+    _lib.check(st, "pasta_hicoo_mttkrp")
+    return out
+
+
+def gather_probe(X: CooTensor, Us: Sequence[torch.Tensor | None], mode: int,
+                 sink: torch.Tensor | None = None) -> torch.Tensor:
+    """Diagnostic: the row gathers of ``mttkrp(X, Us, mode)`` alone (same
+    kernel and launch, no arithmetic into output rows); returns the FP32
+    sink it wrote (one float per thread, meaningless values).  Its time is
+    the gather ceiling of the MTTKRP on this tensor."""
+    X.sort_by_mode(mode)
+    ptrs, dt, R = _factor_ptrs(X, Us, skip=mode)
+    if sink is None:
+        sink = torch.empty(1 << 22, dtype=torch.float32, device=X.device)
+    with torch.cuda.device(X.device):
+        st = _lib.lib().pasta_gather_probe(X.handle, ptrs, pasta_dtype(dt), int(mode), R,
+                                           sink.data_ptr(), sink.numel(), _stream(X.device))
+    _lib.check(st, "pasta_gather_probe")
+    return sink
+
+
 def cp_loss_fwd(X: CooTensor, Us: Sequence[torch.Tensor], mode: int = -1,
                 want_resid: bool = False):
     """Sparse CP least-squares loss over the stored entries (FP64 0-d tensor),

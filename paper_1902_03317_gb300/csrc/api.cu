@@ -11,6 +11,7 @@
 #include <new>
 
 #include "pasta_internal.cuh"
+#include "stream_kernels.cuh"
 
 namespace pasta {
 
@@ -365,6 +366,7 @@ pasta_status pasta_coo_destroy(pasta_coo X) {
     free_copy(X->orig);
     for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(X->sorted[k]);
     for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_fibers(X->fibers[k]);
+    free_hicoo(X->hicoo);
     dev_free(X->partials);
     dev_free(X->als_normsq);
     dev_free(X->scratch);
@@ -497,6 +499,45 @@ pasta_status pasta_mttkrp(pasta_coo X, const void *const *d_U, pasta_dtype u_dty
     }
     return launch_mttkrp(X, X->sorted[mode], d_U, u_dtype, mode, R, d_M,
                          static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_gather_probe(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int mode,
+                                int R, float *d_sink, uint64_t sink_len, void *stream) {
+    if (X && (mode < 0 || mode >= X->order)) {
+        set_error("mode %d out of range", mode);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    pasta_status st = check_factors(X, d_U, u_dtype, R, mode);
+    if (st != PASTA_OK) return st;
+    if (!d_sink || sink_len < (uint64_t)stream::kThreads) {
+        set_error("d_sink is NULL or holds fewer than %d floats", stream::kThreads);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (!X->sorted[mode].present) {
+        set_error("mode %d has no sorted copy (call pasta_coo_sort_by_mode)", mode);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    if (!stream_supported(u_dtype, X->order, R, d_U, mode, d_sink, 2)) {
+        set_error("the gather probe covers the streaming MTTKRP cases only");
+        return PASTA_ERR_UNSUPPORTED;
+    }
+    if (X->nnz == 0) return PASTA_OK;
+    const StoredCopy &c = X->sorted[mode];
+    StreamLaunch l;
+    l.order = X->order;
+    l.R = R;
+    l.dtype = u_dtype;
+    for (int p = 0; p < X->order; ++p) {
+        const int k = (mode + p) % X->order;
+        l.idx[p] = c.idx[k];
+        l.U[p] = d_U[k];
+    }
+    l.val = c.val;
+    l.out = d_sink;
+    l.nnz = X->nnz;
+    l.num_sms = X->num_sms;
+    l.max_blocks = (int)std::min<uint64_t>(sink_len / stream::kThreads, 1u << 30);
+    return launch_stream(stream::kGather, l, static_cast<cudaStream_t>(stream));
 }
 
 pasta_status pasta_cp_loss_fwd(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int R,
@@ -665,6 +706,7 @@ static pasta_status elementwise_output(pasta_coo X, pasta_coo Y, pasta_coo *Z, c
         cudaStreamSynchronize(s);  // earlier work on O may still read what is freed here
         for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_copy(O->sorted[k]);
         for (int k = 0; k < PASTA_MAX_ORDER; ++k) free_fibers(O->fibers[k]);
+        free_hicoo(O->hicoo);
         if (O->als_normsq) {
             dev_free(O->als_normsq);
             O->als_normsq = nullptr;
@@ -779,6 +821,132 @@ pasta_status pasta_ttm(pasta_coo X, int mode, const void *d_U, pasta_dtype u_dty
 pasta_status pasta_ttv(pasta_coo X, int mode, const void *d_v, pasta_dtype v_dtype, void *d_y,
                        void *stream) {
     return pasta_ttm(X, mode, d_v, v_dtype, 1, d_y, stream);
+}
+
+// A shallow copy of X whose stored copies start at entry lo and hold hi - lo
+// entries (the arrays stay X's; nothing is owned).
+static pasta_status range_view(pasta_coo X, uint64_t lo, uint64_t hi, pasta_coo_s *out) {
+    if (lo > hi || hi > X->nnz) {
+        set_error("range [%llu, %llu) outside [0, %llu)", (unsigned long long)lo, (unsigned long long)hi,
+                  (unsigned long long)X->nnz);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (lo % 4 != 0) {
+        set_error("range start %llu is not a multiple of 4 entries", (unsigned long long)lo);
+        return PASTA_ERR_ALIGNMENT;
+    }
+    *out = *X;
+    out->nnz = hi - lo;
+    auto shift = [&](StoredCopy &c) {
+        if (!c.present) return;
+        for (int k = 0; k < X->order; ++k) c.idx[k] += lo;
+        c.val += lo;
+        if (c.perm) c.perm += lo;
+    };
+    shift(out->orig);
+    for (int k = 0; k < X->order; ++k) shift(out->sorted[k]);
+    out->hicoo = HicooCopy{};
+    for (int k = 0; k < PASTA_MAX_ORDER; ++k) out->fibers[k] = FiberTable{};
+    return PASTA_OK;
+}
+
+pasta_status pasta_mttkrp_range(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int mode, int R,
+                                uint64_t lo, uint64_t hi, void *d_M, void *stream) {
+    if (X && (mode < 0 || mode >= X->order)) {
+        set_error("mode %d out of range", mode);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    pasta_status st = check_factors(X, d_U, u_dtype, R, mode);
+    if (st != PASTA_OK) return st;
+    if (!d_M) {
+        set_error("d_M is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (!X->sorted[mode].present) {
+        set_error("mode %d has no sorted copy (call pasta_coo_sort_by_mode)", mode);
+        return PASTA_ERR_NOT_SORTED;
+    }
+    pasta_coo_s V;
+    st = range_view(X, lo, hi, &V);
+    if (st != PASTA_OK) return st;
+    return launch_mttkrp(&V, V.sorted[mode], d_U, u_dtype, mode, R, d_M, static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_cp_loss_fwd_bwd_range(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int R,
+                                         uint64_t lo, uint64_t hi, double *d_loss, const double *d_gscale,
+                                         void *const *d_G, void *stream) {
+    pasta_status st = check_factors(X, d_U, u_dtype, R, -1);
+    if (st != PASTA_OK) return st;
+    if (!d_loss || !d_G) {
+        set_error("d_loss/d_G is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < X->order; ++k) {
+        if (!d_G[k]) {
+            set_error("d_G[%d] is NULL", k);
+            return PASTA_ERR_INVALID_ARG;
+        }
+        if (!X->sorted[k].present) {
+            set_error("mode %d has no sorted copy", k);
+            return PASTA_ERR_NOT_SORTED;
+        }
+    }
+    pasta_coo_s V;
+    st = range_view(X, lo, hi, &V);
+    if (st != PASTA_OK) return st;
+    return launch_cp_loss_fwd_bwd(&V, d_U, u_dtype, R, d_loss, d_gscale, d_G, static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_coo_hicoo(pasta_coo X, int block_bits, uint64_t *nblocks, void *stream) {
+    if (!X || block_bits < 1 || block_bits > 8) {
+        set_error("NULL handle or block_bits out of [1, 8]");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    pasta_status st = build_hicoo(X, block_bits, static_cast<cudaStream_t>(stream));
+    if (st == PASTA_OK && nblocks) *nblocks = X->hicoo.nb;
+    return st;
+}
+
+pasta_status pasta_hicoo_copy_out(pasta_coo X, uint32_t *d_bptr, uint32_t *const *d_binds,
+                                  uint8_t *const *d_einds, float *d_val, void *stream) {
+    if (!X) {
+        set_error("NULL handle");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    const HicooCopy &H = X->hicoo;
+    if (!H.present) {
+        set_error("no HiCOO copy (call pasta_coo_hicoo)");
+        return PASTA_ERR_NOT_SORTED;
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (d_bptr) PASTA_CUDA(cudaMemcpyAsync(d_bptr, H.bptr, (H.nb + 1) * 4, cudaMemcpyDeviceToDevice, s));
+    for (int k = 0; k < X->order; ++k) {
+        if (d_binds && d_binds[k] && H.nb)
+            PASTA_CUDA(cudaMemcpyAsync(d_binds[k], H.binds[k], H.nb * 4, cudaMemcpyDeviceToDevice, s));
+        if (d_einds && d_einds[k] && X->nnz)
+            PASTA_CUDA(cudaMemcpyAsync(d_einds[k], H.einds[k], X->nnz, cudaMemcpyDeviceToDevice, s));
+    }
+    if (d_val && X->nnz) PASTA_CUDA(cudaMemcpyAsync(d_val, H.val, X->nnz * 4, cudaMemcpyDeviceToDevice, s));
+    return PASTA_OK;
+}
+
+pasta_status pasta_hicoo_mttkrp(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int mode, int R,
+                                void *d_M, void *stream) {
+    if (X && (mode < 0 || mode >= X->order)) {
+        set_error("mode %d out of range", mode);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    pasta_status st = check_factors(X, d_U, u_dtype, R, mode);
+    if (st != PASTA_OK) return st;
+    if (!d_M) {
+        set_error("d_M is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (!X->hicoo.present) {
+        set_error("no HiCOO copy (call pasta_coo_hicoo)");
+        return PASTA_ERR_NOT_SORTED;
+    }
+    return launch_hicoo_mttkrp(X, d_U, u_dtype, mode, R, d_M, static_cast<cudaStream_t>(stream));
 }
 
 pasta_status pasta_set_grid_cap(int max_blocks) {

@@ -65,6 +65,23 @@ struct FiberTable {
     bool present = false;
 };
 
+// HiCOO copy (hicoo.cu): blocks of 2^bits cells per mode, one copy for
+// every mode.
+constexpr uint32_t kHTile = 512;  // entries per work tile of the HiCOO MTTKRP
+struct HicooCopy {
+    int bits = 0;
+    uint64_t nb = 0;                     // nonempty blocks
+    uint64_t ntiles = 0;                 // kHTile-entry tiles
+    uint32_t *bptr = nullptr;            // nb + 1: first entry of each block, then nnz
+    uint32_t *binds[kMaxOrder] = {};     // nb each: block coordinates
+    uint8_t *einds[kMaxOrder] = {};      // per entry (padded): offset inside the block
+    float *val = nullptr;                // per entry (padded)
+    uint32_t *tile_block = nullptr;      // ntiles: block holding each tile's first entry
+    void *block = nullptr;               // einds, val (and the build's permutation)
+    void *bblock = nullptr;              // bptr, binds, tile_block
+    bool present = false;
+};
+
 }  // namespace pasta
 
 struct pasta_coo_s {
@@ -82,6 +99,7 @@ struct pasta_coo_s {
     void *scratch = nullptr;       // grow-only scratch (handle_scratch)
     size_t scratch_bytes = 0;
     pasta::FiberTable fibers[PASTA_MAX_ORDER];  // per mode, built by pasta_coo_fibers
+    pasta::HicooCopy hicoo;                     // built by pasta_coo_hicoo
 };
 
 namespace pasta {
@@ -133,6 +151,14 @@ pasta_status validate_coo(const pasta_coo_s *X, void *stream, uint64_t *bad_inde
 pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t stream);
 // Computes the mode's sorted-copy permutation if the sort left it out.
 pasta_status ensure_perm(pasta_coo_s *X, int mode, cudaStream_t stream);
+// The mode sort's stable LSD radix sort on other keys: `make` writes n keys
+// (bits [0, used) significant) and n 32-bit payloads into the two device
+// buffers it is given (the handle's scratch); the sorted payloads land in
+// payload_out and *keys_sorted points at the sorted keys (in the scratch,
+// valid until its next use).
+using MakeKeysFn = pasta_status (*)(void *ctx, uint64_t *keys, uint32_t *payload, cudaStream_t s);
+pasta_status radix_sort_keys(pasta_coo_s *X, uint64_t n, int used, MakeKeysFn make, void *ctx,
+                             uint32_t *payload_out, const uint64_t **keys_sorted, cudaStream_t s);
 
 // every_row_touched: every row of M has at least one entry (the TTM view,
 // whose rows are fibers), so the streaming kernel's output needs zeros only
@@ -209,6 +235,12 @@ pasta_status build_fibers(pasta_coo_s *X, int mode, cudaStream_t stream);
 void free_fibers(pasta::FiberTable &F);
 pasta_status launch_ttm(pasta_coo_s *X, int mode, const void *U, pasta_dtype dt, int R, void *Y,
                         cudaStream_t stream);
+
+// HiCOO copy and its MTTKRP (hicoo.cu).
+pasta_status build_hicoo(pasta_coo_s *X, int bits, cudaStream_t stream);
+void free_hicoo(HicooCopy &H);
+pasta_status launch_hicoo_mttkrp(const pasta_coo_s *X, const void *const *U, pasta_dtype dt, int mode, int R,
+                                 void *M, cudaStream_t stream);
 
 pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,
                             uint64_t n, const double *scale, cudaStream_t stream);

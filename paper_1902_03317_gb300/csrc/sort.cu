@@ -439,10 +439,11 @@ GatherDst decode_spec(const pasta_coo_s *X, const KeySpec &ks, const StoredCopy 
 // low > 0 when srcc is already ordered by the low bits (see sort_copy).  The
 // sorted payload lands in payload_out (nnz words); *keys_sorted points at the
 // sorted keys inside the handle's scratch (valid until its next use).
-pasta_status radix_sort(pasta_coo_s *X, const StoredCopy &srcc, const KeySpec &ks, int low, int used,
-                        bool payload_val, uint32_t *payload_out, const uint64_t **keys_sorted,
-                        cudaStream_t s) {
-    const uint64_t n = X->nnz;
+// The passes of the radix sort over keys and payloads that `make` writes
+// into the scratch (see radix_sort).
+template <typename Make>
+pasta_status radix_core(pasta_coo_s *X, uint64_t n, int low, int used, Make make, uint32_t *payload_out,
+                        const uint64_t **keys_sorted, cudaStream_t s) {
     // digits of at most 9 bits, balanced over the fewest passes: 57 bits take
     // 7 passes (one of 9 bits), 64 take 8 of 8
     const int bits = used - low;
@@ -468,9 +469,8 @@ pasta_status radix_sort(pasta_coo_s *X, const StoredCopy &srcc, const KeySpec &k
                                     (int)kScatterSmem));
     PASTA_CUDA(cudaFuncSetAttribute(k_scatter<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)kScatterSmem));
-    const CooView src = view_of(X, srcc);
-    const int gblocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16);
-    k_make_keys<<<gblocks, 256, 0, s>>>(src, ks, kb[0], vb[0], payload_val);
+    st = make(kb[0], vb[0]);
+    if (st != PASTA_OK) return st;
     int shift = low;
     for (int p = 0; p < passes; ++p) {
         const int width = bits / passes + (p < bits % passes ? 1 : 0);  // 1..9 bits
@@ -493,6 +493,22 @@ pasta_status radix_sort(pasta_coo_s *X, const StoredCopy &srcc, const KeySpec &k
     PASTA_CUDA(cudaGetLastError());
     *keys_sorted = kb[passes % 2];
     return PASTA_OK;
+}
+
+pasta_status radix_sort(pasta_coo_s *X, const StoredCopy &srcc, const KeySpec &ks, int low, int used,
+                        bool payload_val, uint32_t *payload_out, const uint64_t **keys_sorted,
+                        cudaStream_t s) {
+    const uint64_t n = X->nnz;
+    const CooView src = view_of(X, srcc);
+    const int gblocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16);
+    return radix_core(
+        X, n, low, used,
+        [&](uint64_t *keys, uint32_t *payload) -> pasta_status {
+            k_make_keys<<<gblocks, 256, 0, s>>>(src, ks, keys, payload, payload_val);
+            PASTA_CUDA(cudaGetLastError());
+            return PASTA_OK;
+        },
+        payload_out, keys_sorted, s);
 }
 
 bool key_holds_all(const GatherDst &gd, int order) {
@@ -542,6 +558,14 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return cuda_fail(le, "sort kernels");
     return PASTA_OK;
+}
+
+pasta_status radix_sort_keys(pasta_coo_s *X, uint64_t n, int used, MakeKeysFn make, void *ctx,
+                             uint32_t *payload_out, const uint64_t **keys_sorted, cudaStream_t s) {
+    if (n == 0) return PASTA_OK;
+    return radix_core(
+        X, n, 0, used, [&](uint64_t *keys, uint32_t *payload) { return make(ctx, keys, payload, s); },
+        payload_out, keys_sorted, s);
 }
 
 pasta_status ensure_perm(pasta_coo_s *X, int mode, cudaStream_t s) {

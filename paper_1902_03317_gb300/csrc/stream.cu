@@ -35,6 +35,7 @@ pasta_status launch_stream(int kind, const StreamLaunch &l, cudaStream_t s) {
         case stream::kMttkrp: return launch_stream_mttkrp(l, s);
         case stream::kLossFwd: return launch_stream_loss_fwd(l, s);
         case stream::kLossBwd: return launch_stream_loss_bwd(l, s);
+        case stream::kGather: return launch_stream_gather(l, s);
     }
     return PASTA_ERR_UNSUPPORTED;
 }

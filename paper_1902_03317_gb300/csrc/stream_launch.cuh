@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(256) k_zero_tile_end_rows(const uint32_t *idx0
 // two blocks' budget.
 template <typename T, int N, int KIND>
 constexpr int min_blocks() {
+    if (KIND == stream::kGather) return min_blocks<T, N, stream::kMttkrp>();  // MTTKRP's launch
     if (N == 2) return 4;
     if (N != 3) return 2;
     if (KIND == stream::kLossBwd) return sizeof(T) == 4 ? 4 : 3;  // with the late row-0 load
@@ -63,6 +64,7 @@ constexpr int row0_late() {
 // L); LC = 0 reads it from the arguments.
 template <typename T, int N, int KIND, int LC>
 pasta_status run(const StreamLaunch &l, cudaStream_t s) {
+    static_assert(KIND != stream::kGather || LC == 0, "the gather kind takes its lane count at run time");
     constexpr int MINB = min_blocks<T, N, KIND>();
     Args<T, N> a{};
     for (int p = 0; p < N; ++p) {
@@ -117,7 +119,7 @@ pasta_status run(const StreamLaunch &l, cudaStream_t s) {
 // measurable and keeps one instantiation per type and order.
 template <typename T, int N, int KIND>
 pasta_status by_lanes(const StreamLaunch &l, cudaStream_t s) {
-    if constexpr (KIND == stream::kMttkrp) {
+    if constexpr (KIND == stream::kMttkrp || KIND == stream::kGather) {
         return run<T, N, KIND, 0>(l, s);
     } else {
         switch (l.R * (int)sizeof(T) / 16) {
@@ -134,7 +136,7 @@ template <typename T, int KIND>
 pasta_status by_order(const StreamLaunch &l, cudaStream_t s) {
     switch (l.order) {
         case 2:  // MTTKRP only (TTM/TTV run as an order-2 MTTKRP)
-            if constexpr (KIND == stream::kMttkrp) return by_lanes<T, 2, KIND>(l, s);
+            if constexpr (KIND == stream::kMttkrp || KIND == stream::kGather) return by_lanes<T, 2, KIND>(l, s);
             return PASTA_ERR_UNSUPPORTED;
         case 3: return by_lanes<T, 3, KIND>(l, s);
         case 4: return by_lanes<T, 4, KIND>(l, s);
@@ -159,5 +161,6 @@ pasta_status by_type(const StreamLaunch &l, cudaStream_t s) {
 pasta_status launch_stream_mttkrp(const StreamLaunch &l, cudaStream_t s);
 pasta_status launch_stream_loss_fwd(const StreamLaunch &l, cudaStream_t s);
 pasta_status launch_stream_loss_bwd(const StreamLaunch &l, cudaStream_t s);
+pasta_status launch_stream_gather(const StreamLaunch &l, cudaStream_t s);
 
 }  // namespace pasta

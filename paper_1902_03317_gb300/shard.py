@@ -9,9 +9,12 @@ rows with atomics or per-thread private outputs plus a global reduction
     to the start of an output row, so every rank owns a disjoint block of
     output rows and no reduction is needed (the rows are gathered if a
     consumer needs all of them);
-  * arbitrary ranges (`even_ranges`) with a sum all-reduce of the partial
-    outputs: the paper's privatization at GPU scale, and the form the loss
-    gradient uses (data parallelism over entries).
+  * arbitrary ranges (`even_ranges`, or `aligned_ranges` whose cuts are
+    multiples of 4 entries, as the library's range calls
+    pasta_mttkrp_range / pasta_cp_loss_fwd_bwd_range need) with a sum
+    all-reduce of the partial outputs: the paper's privatization at GPU
+    scale, and the form the loss gradient uses (data parallelism over
+    entries).
 """
 from __future__ import annotations
 
@@ -47,4 +50,15 @@ def row_aligned_ranges(sorted_rows: Sequence[int] | np.ndarray, parts: int) -> l
             c = int(np.searchsorted(rows, rows[c - 1], side="right"))
         cuts.append(min(max(c, cuts[-1]), nnz))
     cuts.append(nnz)
+    return [(cuts[p], cuts[p + 1]) for p in range(parts)]
+
+
+def aligned_ranges(nnz: int, parts: int, align: int = 4) -> list[tuple[int, int]]:
+    """`parts` contiguous ranges covering [0, nnz), every cut a multiple of
+    `align` entries, sizes as equal as that allows (the last range takes the
+    remainder; ranges may be empty when nnz < parts * align)."""
+    if parts < 1 or align < 1:
+        raise ValueError("parts and align must be >= 1")
+    units = -(-nnz // align)
+    cuts = [min(nnz, ((units * p) // parts) * align) for p in range(parts)] + [nnz]
     return [(cuts[p], cuts[p + 1]) for p in range(parts)]

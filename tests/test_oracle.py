@@ -316,3 +316,24 @@ def test_pins_catch_planted_loss_mistakes(golden_worked, mistake):
     assert passes(_loss_grad_loop)
     assert passes(lambda *a: (oracle.cp_loss(*a), oracle.cp_grad(*a)))
     assert not passes(lambda *a: _loss_grad_loop(*a, mistake=mistake))
+
+
+# ---------------------------------------------------------------------------
+# The multicore CPU baseline (privatization MTTKRP of Sec. 5.3, FP32) is a
+# timed baseline, not a reference; it must still compute the same MTTKRP.
+
+@pytest.mark.parametrize("threads", [1, 3, 0])
+def test_cpu_privatized_baseline_matches_oracle(threads):
+    rng = np.random.default_rng(5)
+    dims = (40, 30, 20, 6)
+    nnz = 3000
+    idx = [rng.integers(0, d, nnz).astype(np.uint32) for d in dims]
+    val = rng.standard_normal(nnz)
+    U = [rng.standard_normal((d, 8)) for d in dims]
+    Uf = [u.astype(np.float32) for u in U]
+    for n in range(len(dims)):
+        ref = oracle.mttkrp(dims, idx, val.astype(np.float32).astype(np.float64),
+                            [u.astype(np.float64) for u in Uf], n, 8)
+        got = oracle.mttkrp_privatized(dims, idx, val, Uf, n, threads=threads)
+        assert got.dtype == np.float32
+        assert np.linalg.norm(got - ref) / np.linalg.norm(ref) < 1e-5
