@@ -62,3 +62,51 @@ def aligned_ranges(nnz: int, parts: int, align: int = 4) -> list[tuple[int, int]
     units = -(-nnz // align)
     cuts = [min(nnz, ((units * p) // parts) * align) for p in range(parts)] + [nnz]
     return [(cuts[p], cuts[p + 1]) for p in range(parts)]
+
+
+def step_range(nnz: int, world: int, rank: int) -> tuple[int, int]:
+    """The range of stored positions rank `rank` of `world` takes in every
+    sorted copy for a sharded step (the cuts of `aligned_ranges`)."""
+    return aligned_ranges(nnz, world)[rank]
+
+
+def boundary_rows(first_row: int, last_row: int, device="cpu", group=None):
+    """The output rows that ranges can share: the union over ranks of each
+    range's first and last rows (first_row / last_row of this rank's range,
+    -1 for an empty range), as an int64 tensor on `device`.  Only these rows
+    can receive contributions from more than one rank.  Collective (one
+    all-gather)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size(group) if dist.is_initialized() else 1
+    ends = torch.tensor([first_row, last_row], dtype=torch.int64, device=device)
+    if world == 1:
+        rows = sorted({r for r in (first_row, last_row) if r >= 0})
+    else:
+        allends = [torch.empty_like(ends) for _ in range(world)]
+        dist.all_gather(allends, ends, group=group)
+        rows = sorted({int(r) for t in allends for r in t.tolist() if r >= 0})
+    return torch.tensor(rows, dtype=torch.int64, device=device)
+
+
+def sum_rows(M, rows, group=None) -> None:
+    """Sum the rows `rows` of every rank's partial output M in place (one
+    all-reduce of those rows only).  Collective."""
+    import torch.distributed as dist
+    if rows.numel() == 0 or not dist.is_initialized() or dist.get_world_size(group) == 1:
+        return
+    sub = M.index_select(0, rows).contiguous()
+    dist.all_reduce(sub, group=group)
+    M.index_copy_(0, rows, sub)
+
+
+def complete_boundary_rows(M, first_row: int, last_row: int, group=None) -> None:
+    """Finish a range-split output in place: M is this rank's partial output
+    (its range's contributions; rows it does not reach are 0) and
+    first_row / last_row are the output rows of its range's first and last
+    entries (-1 for an empty range).  Only rows at range ends can be shared
+    by several ranks, so those rows' partials are summed across ranks
+    (boundary_rows, then sum_rows).  Afterwards every rank holds the
+    complete value of every row its range reaches; together the ranks hold
+    the whole output.  Collective: every rank of `group` must call it."""
+    sum_rows(M, boundary_rows(first_row, last_row, M.device, group), group)

@@ -109,3 +109,78 @@ def test_two_gloo_ranks_match_whole_tensor():
     for g, r in zip(G, oracle.cp_grad(dims, idx, val, U)):
         np.testing.assert_allclose(g, r, rtol=1e-12, atol=1e-12)
     assert abs(loss - oracle.cp_loss(dims, idx, val, U)) < 1e-9 * max(1.0, loss)
+
+
+def _worker_step(rank, world, port, results):
+    """The sharded step of bench.py on gloo ranks with oracle arithmetic:
+    each rank takes shard.step_range of every mode's sorted copy, computes
+    its partial MTTKRP for every mode and its partial loss and gradients, and
+    completes the range-end rows with shard.complete_boundary_rows."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        dims, idx, val, U = _tensor()
+        nnz = len(val)
+        lo, hi = shard.step_range(nnz, world, rank)
+        Ms, Gs, loss = [], [], 0.0
+        for n in range(len(dims)):
+            p = oracle.sort_perm(idx, n)
+            sidx = [ix[p][lo:hi] for ix in idx]
+            sval = val[p][lo:hi]
+            M = torch.from_numpy(oracle.mttkrp(dims, sidx, sval, U, n))
+            first = int(sidx[n][0]) if hi > lo else -1
+            last = int(sidx[n][-1]) if hi > lo else -1
+            shard.complete_boundary_rows(M, first, last)
+            G = torch.from_numpy(oracle.cp_grad(dims, sidx, sval, U)[n])
+            shard.complete_boundary_rows(G, first, last)
+            reach = np.unique(sidx[n])
+            Ms.append((M.numpy()[reach], reach))
+            Gs.append((G.numpy()[reach], reach))
+            if n == 0:
+                loss = oracle.cp_loss(dims, sidx, sval, U)
+        lt = torch.tensor([loss], dtype=torch.float64)
+        dist.all_reduce(lt)
+        results.put((rank, Ms, Gs, float(lt[0])))
+    finally:
+        dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_step_matches_whole_tensor(world):
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker_step, args=(r, world, port, q)) for r in range(world)]
+    for pr in procs:
+        pr.start()
+    got = [q.get(timeout=180) for _ in range(world)]
+    for pr in procs:
+        pr.join(timeout=60)
+        assert pr.exitcode == 0
+    dims, idx, val, U = _tensor()
+    refG = oracle.cp_grad(dims, idx, val, U)
+    for rank, Ms, Gs, loss in got:
+        assert abs(loss - oracle.cp_loss(dims, idx, val, U)) < 1e-9 * max(1.0, loss)
+        for n in range(len(dims)):
+            ref = oracle.mttkrp(dims, idx, val, U, n)
+            m, rows = Ms[n]
+            np.testing.assert_allclose(m, ref[rows], rtol=1e-12, atol=1e-12)
+            g, rows = Gs[n]
+            np.testing.assert_allclose(g, refG[n][rows], rtol=1e-12, atol=1e-12)
+    # together the ranks reach every row that has an entry
+    for n in range(len(dims)):
+        reached = set()
+        for _, Ms, _, _ in got:
+            reached |= set(Ms[n][1].tolist())
+        assert reached == set(np.unique(idx[n]).tolist())
+
+
+def test_aligned_ranges_cover():
+    for nnz in (0, 1, 3, 4, 10, 4001, 100_003):
+        for parts in (1, 2, 3, 8):
+            rs = shard.aligned_ranges(nnz, parts)
+            assert rs[0][0] == 0 and rs[-1][1] == nnz and len(rs) == parts
+            for (a, b), (c, d) in zip(rs, rs[1:]):
+                assert b == c and a <= b and a % 4 == 0
+            assert max(b - a for a, b in rs) - min(b - a for a, b in rs) <= 4 * 2 or nnz < 8 * parts
