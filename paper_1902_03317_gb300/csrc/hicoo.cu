@@ -269,7 +269,7 @@ pasta_status build_hicoo(pasta_coo_s *X, int bits, cudaStream_t s) {
     const size_t e_b = ((size_t)X->nnz_pad + 255) & ~(size_t)255;
     const size_t v_b = ((size_t)X->nnz_pad * 4 + 255) & ~(size_t)255;
     H.bits = bits;
-    cudaError_t e = dev_malloc(&H.block, e_b * N + v_b + (((size_t)n * 4 + 255) & ~(size_t)255), s);
+    cudaError_t e = dev_malloc(&H.block, e_b * N + v_b, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         H = HicooCopy{};
@@ -279,7 +279,6 @@ pasta_status build_hicoo(pasta_coo_s *X, int bits, cudaStream_t s) {
     char *blk = static_cast<char *>(H.block);
     for (int k = 0; k < N; ++k) H.einds[k] = reinterpret_cast<uint8_t *>(blk + e_b * k);
     H.val = reinterpret_cast<float *>(blk + e_b * N);
-    uint32_t *perm = reinterpret_cast<uint32_t *>(blk + e_b * N + v_b);
     PASTA_CUDA(cudaMemsetAsync(H.block, 0, e_b * N + v_b, s));  // padding words read by 4-entry loads
     if (n == 0) {
         H.nb = 0;
@@ -296,25 +295,31 @@ pasta_status build_hicoo(pasta_coo_s *X, int bits, cudaStream_t s) {
         return PASTA_OK;
     }
 
-    KeyCtx kc{view_of(X, X->orig), ks, (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16)};
-    const uint64_t *keys = nullptr;
-    pasta_status st = radix_sort_keys(X, n, used, make_hkeys, &kc, perm, &keys, s);
-    if (st != PASTA_OK) {
-        free_hicoo(H);
-        return st;
-    }
-    // block heads: counts per tile, scan, one synchronisation for nb
+    // build temporaries: the permutation, per-tile head counts and offsets, the block count
     const uint32_t ntile = (uint32_t)((n + kTile - 1) / kTile);
+    const size_t perm_b = ((size_t)n * 4 + 255) & ~(size_t)255;
     void *tmp = nullptr;
-    e = dev_malloc(&tmp, (size_t)ntile * 8 + 64, s);
+    e = dev_malloc(&tmp, perm_b + (size_t)ntile * 8 + 64, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         free_hicoo(H);
         return PASTA_ERR_NOMEM;
     }
-    uint32_t *counts = static_cast<uint32_t *>(tmp);
+    uint32_t *perm = static_cast<uint32_t *>(tmp);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(static_cast<char *>(tmp) + perm_b);
     uint32_t *offsets = counts + ntile;
-    uint64_t *total = reinterpret_cast<uint64_t *>(static_cast<char *>(tmp) + (((size_t)ntile * 8 + 7) & ~(size_t)7));
+    uint64_t *total =
+        reinterpret_cast<uint64_t *>(static_cast<char *>(tmp) + perm_b + (((size_t)ntile * 8 + 7) & ~(size_t)7));
+    KeyCtx kc{view_of(X, X->orig), ks, (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16)};
+    const uint64_t *keys = nullptr;
+    pasta_status st = radix_sort_keys(X, n, used, make_hkeys, &kc, perm, &keys, s);
+    if (st != PASTA_OK) {
+        cudaStreamSynchronize(s);
+        dev_free(tmp);
+        free_hicoo(H);
+        return st;
+    }
+    // block heads: counts per tile, scan, one synchronisation for nb
     uint64_t nb = 0;
     k_hhead_count<<<ntile, kThreads, 0, s>>>(keys, n, ks.elem_keep, counts);
     k_hscan<<<1, 1024, 0, s>>>(counts, ntile, offsets, total);

@@ -77,7 +77,7 @@ struct HicooCopy {
     uint8_t *einds[kMaxOrder] = {};      // per entry (padded): offset inside the block
     float *val = nullptr;                // per entry (padded)
     uint32_t *tile_block = nullptr;      // ntiles: block holding each tile's first entry
-    void *block = nullptr;               // einds, val (and the build's permutation)
+    void *block = nullptr;               // einds, val
     void *bblock = nullptr;              // bptr, binds, tile_block
     bool present = false;
 };
