@@ -269,7 +269,10 @@ pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype 
  * once) race and give wrong losses; calls in sequence on one stream are safe.
  * The first call on a device looks up the array's device address for that
  * device (cudaGetSymbolAddress, which may load the library's device code), so
- * make the first call on each device before any stream capture.
+ * make the first call on each device before any stream capture.  The address
+ * is kept for the life of the process: after cudaDeviceReset on a device the
+ * library's device code is reloaded and the array may move, so this entry
+ * point must not be used on that device again in the same process.
  */
 #define PASTA_NOALLOC_MAX_PARTIALS 4096
 

@@ -238,16 +238,32 @@ __device__ __forceinline__ void close_run(const Ctx<T, N, KIND> &c,
 // R0L (loss kinds): 0 = position 0's row, needed where a run starts, is
 // gathered with the others in phase A (a register row per entry); 1 = it is
 // loaded in phase B when the run changes (fewer registers, a dependent load).
+// One batch's staged inputs between its two phases: position 0's indices and
+// the values of the four entries, and the rows gathered in phase A.
+template <int N, int NR>
+struct Staged {
+    uint32_t i0[4];
+    float v[4];
+    uint4 rows[4][NR];
+    bool need0[4];
+};
+
+template <int N, int KIND, int R0L>
+struct Shape {
+    static constexpr bool MT = (KIND == kMttkrp || KIND == kGather);
+    static constexpr int P0 = (MT || R0L) ? 1 : 0;  // first position gathered in phase A
+    static constexpr int NR = N - P0;               // rows gathered per entry in phase A
+};
+
+// Phase A of the four entries held at position `src` of the group's chunk:
+// indices and values from shared memory, then every gathered row (position
+// 0, loss kinds, only where the run changes; prev0 = the row of the entry
+// before the batch).  CHECK = false when all four are real entries.
 template <bool CHECK, int R0L, typename T, int N, int KIND>
-__device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
-                                      GroupState<Ctx<T, N, KIND>::VEC> &s, const uint32_t *sb,
-                                      int AS, int src, int lim, uint64_t pos) {
-    constexpr int VEC = Ctx<T, N, KIND>::VEC;
-    constexpr bool MT = (KIND == kMttkrp || KIND == kGather);
-    constexpr int P0 = (MT || R0L) ? 1 : 0;  // first position gathered in phase A
-    constexpr int NR = N - P0;               // rows gathered per entry in phase A
+__device__ __forceinline__ void batch_load(const Ctx<T, N, KIND> &c, uint32_t prev0, const uint32_t *sb, int AS,
+                                           int src, int lim, Staged<N, Shape<N, KIND, R0L>::NR> &b) {
+    constexpr int P0 = Shape<N, KIND, R0L>::P0;
     uint32_t iw[N][4];
-    float vw[4];
 #pragma unroll
     for (int k = 0; k < N; ++k) {
         const uint4 w = *reinterpret_cast<const uint4 *>(sb + k * AS + 4 * src);
@@ -255,34 +271,43 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
     }
     {
         const float4 w = *reinterpret_cast<const float4 *>(sb + N * AS + 4 * src);
-        vw[0] = w.x; vw[1] = w.y; vw[2] = w.z; vw[3] = w.w;
+        b.v[0] = w.x; b.v[1] = w.y; b.v[2] = w.z; b.v[3] = w.w;
     }
-    // Phase A: all gathered rows of the four entries.  Position 0 (loss kinds)
-    // is loaded only where the run changes.
-    uint4 rows[4][NR];
-    bool need0[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
+        b.i0[q] = iw[0][q];
         const bool ok = !CHECK || q < lim;
-        need0[q] = ok && iw[0][q] != (q == 0 ? s.cur : iw[0][q - 1]);
+        b.need0[q] = ok && iw[0][q] != (q == 0 ? prev0 : iw[0][q - 1]);
 #pragma unroll
         for (int p = P0; p < N; ++p) {
             const uint4 *ptr = reinterpret_cast<const uint4 *>(c.ub[p] + (uint64_t)iw[p][q] * c.stride);
             if (p == 0) {
-                if (need0[q]) rows[q][0] = ld_row(ptr, c.pol_rows);
-
+                if (b.need0[q]) b.rows[q][0] = ld_row(ptr, c.pol_rows);
             } else if (CHECK) {
-                rows[q][p - P0] = ok ? ld_row(ptr, c.pol_rows) : make_uint4(0u, 0u, 0u, 0u);
+                b.rows[q][p - P0] = ok ? ld_row(ptr, c.pol_rows) : make_uint4(0u, 0u, 0u, 0u);
             } else {
-                rows[q][p - P0] = ld_row(ptr, c.pol_rows);
+                b.rows[q][p - P0] = ld_row(ptr, c.pol_rows);
             }
         }
     }
-    // Phase B
+}
+
+// Phase B: the four entries' arithmetic in stream order.
+// R0L (loss kinds): 0 = position 0's row, needed where a run starts, was
+// gathered in phase A (a register row per entry); 1 = it is loaded here when
+// the run changes (fewer registers, a dependent load).
+template <bool CHECK, int R0L, typename T, int N, int KIND>
+__device__ __forceinline__ void batch_compute(const Ctx<T, N, KIND> &c, GroupState<Ctx<T, N, KIND>::VEC> &s,
+                                              const Staged<N, Shape<N, KIND, R0L>::NR> &b, int lim,
+                                              uint64_t pos) {
+    constexpr int VEC = Ctx<T, N, KIND>::VEC;
+    constexpr bool MT = Shape<N, KIND, R0L>::MT;
+    constexpr int P0 = Shape<N, KIND, R0L>::P0;
+    constexpr int NR = Shape<N, KIND, R0L>::NR;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const bool ok = !CHECK || q < lim;
-        const bool changed = ok && iw[0][q] != s.cur;
+        const bool changed = ok && b.i0[q] != s.cur;
         if (KIND != kLossFwd && KIND != kGather) {
             if (__any_sync(kFull, changed)) {
                 if (changed) {
@@ -292,49 +317,49 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
                 }
             }
         }
-        if (changed) s.cur = iw[0][q];
+        if (changed) s.cur = b.i0[q];
         if constexpr (!MT && R0L) {
-            if (need0[q])
-                s.row0 = ld_row(reinterpret_cast<const uint4 *>(c.ub[0] + (uint64_t)iw[0][q] * c.stride),
+            if (b.need0[q])
+                s.row0 = ld_row(reinterpret_cast<const uint4 *>(c.ub[0] + (uint64_t)b.i0[q] * c.stride),
                                 c.pol_rows);
-        } else if (!MT && need0[q]) {
-            s.row0 = rows[q][0];
+        } else if (!MT && b.need0[q]) {
+            s.row0 = b.rows[q][0];
         }
         float p[VEC], r[VEC];
         if constexpr (KIND == kGather) {
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-                widen<T, VEC>(rows[q][k], r);
+                widen<T, VEC>(b.rows[q][k], r);
                 if (ok) {
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) s.acc[e] += r[e];
                 }
             }
         } else if constexpr (KIND == kMttkrp && NR == 1) {  // order 2: val times one row
-            widen<T, VEC>(rows[q][0], r);
-            if (ok) v_fma_s<VEC>(s.acc, vw[q], r);
+            widen<T, VEC>(b.rows[q][0], r);
+            if (ok) v_fma_s<VEC>(s.acc, b.v[q], r);
         } else if (KIND == kMttkrp) {
-            widen<T, VEC>(rows[q][0], r);
-            v_scale<VEC>(p, vw[q], r);
+            widen<T, VEC>(b.rows[q][0], r);
+            v_scale<VEC>(p, b.v[q], r);
 #pragma unroll
             for (int k = 1; k < NR - 1; ++k) {
-                widen<T, VEC>(rows[q][k], r);
+                widen<T, VEC>(b.rows[q][k], r);
                 v_mul<VEC>(p, r);
             }
-            widen<T, VEC>(rows[q][NR - 1], r);
+            widen<T, VEC>(b.rows[q][NR - 1], r);
             if (ok) v_fma<VEC>(s.acc, p, r);
         } else {
             // p = prod over positions 1..N-1; model = sum_r p * row0
-            widen<T, VEC>(rows[q][1 - P0], p);
+            widen<T, VEC>(b.rows[q][1 - P0], p);
 #pragma unroll
             for (int k = 2; k < N; ++k) {
-                widen<T, VEC>(rows[q][k - P0], r);
+                widen<T, VEC>(b.rows[q][k - P0], r);
                 v_mul<VEC>(p, r);
             }
             widen<T, VEC>(s.row0, r);
             float part = v_dot<VEC>(p, r);
             for (int o = c.L >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o, c.L);
-            const float e_m = vw[q] - part;
+            const float e_m = b.v[q] - part;
             if (KIND == kLossFwd) {
                 if (ok && c.lig == 0) {
                     // FP32 within a chunk (at most 4L <= 128 positive terms,
@@ -352,6 +377,15 @@ __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c,
             }
         }
     }
+}
+
+// One batch, both phases.
+template <bool CHECK, int R0L, typename T, int N, int KIND>
+__device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c, GroupState<Ctx<T, N, KIND>::VEC> &s,
+                                      const uint32_t *sb, int AS, int src, int lim, uint64_t pos) {
+    Staged<N, Shape<N, KIND, R0L>::NR> b;
+    batch_load<CHECK, R0L>(c, s.cur, sb, AS, src, lim, b);
+    batch_compute<CHECK, R0L>(c, s, b, lim, pos);
 }
 
 // LC: lanes per entry fixed at compile time (0 = read from Args), which turns
