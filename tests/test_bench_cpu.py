@@ -66,3 +66,25 @@ def test_sort_byte_model():
     assert r["alg_bytes_per_mode"] == alg
     assert r["achieved_gbs"] == pytest.approx(alg / (4 / 3 * 1e-3) / 1e9, rel=1e-3)
     assert r["frac"] == pytest.approx(r["achieved_gbs"] / 1000.0, rel=1e-3)
+
+
+def test_mttkrp_byte_model():
+    # order 3, R = 32, FP32 factors: COO stream 16 B per entry, the other modes'
+    # touched rows once, the FP32 output once
+    touched = [900, 500, 300]
+    dims = [1000, 600, 400]
+    b = bench.mttkrp_alg_bytes(10_000, 3, 32, 4, touched, dims, 1)
+    assert b == 10_000 * 16 + (900 + 300) * 32 * 4 + 600 * 32 * 4
+    # 16-bit factors halve the row bytes, not the stream or the FP32 output
+    b16 = bench.mttkrp_alg_bytes(10_000, 3, 32, 2, touched, dims, 1)
+    assert b16 == 10_000 * 16 + (900 + 300) * 32 * 2 + 600 * 32 * 4
+
+
+def test_sharded_ranges_cover_every_copy_position():
+    from paper_1902_03317_gb300 import shard
+    for nnz in (0, 5, 100_003):
+        for world in (1, 2, 3, 8):
+            got = [shard.step_range(nnz, world, r) for r in range(world)]
+            assert got == shard.aligned_ranges(nnz, world)
+            covered = sum(hi - lo for lo, hi in got)
+            assert covered == nnz and all(lo % 4 == 0 for lo, _ in got)

@@ -114,3 +114,19 @@ def test_errors():
         pasta.hicoo_mttkrp(X, dev5, 1)
     assert e.value.name == "PASTA_ERR_UNSUPPORTED"
     X.close()
+
+
+@pytest.mark.parametrize("dtype,R", [(torch.float32, 4), (torch.float32, 8), (torch.float32, 128),
+                                     (torch.bfloat16, 8), (torch.bfloat16, 256), (torch.float16, 32)])
+def test_rank_and_type_sweep(dtype, R):
+    """The lane-group geometry from 1 lane per row (FP32 R = 4) to 32 (BF16
+    R = 256), and FP16 factors."""
+    Xh = G.synth.generate(G.small("zipf4d", 30_000, (900, 800, 70, 20)))
+    idx, val = G.host(Xh)
+    master, dev, rounded = G.factors(Xh.dims, R, 55, dtype)
+    X = G.to_device(Xh)
+    pasta.hicoo(X, 4)
+    for n in range(4):
+        M = pasta.hicoo_mttkrp(X, dev, n).cpu().numpy()
+        assert G.rel_err(M, oracle.mttkrp(Xh.dims, idx, val, rounded, n, R)) < G.FP32_TOL, n
+    X.close()
