@@ -107,6 +107,10 @@ template <int K> __device__ __forceinline__ void cp_wait() {
 #define PASTA_STREAM_F2 1
 #endif
 constexpr bool kF2 = PASTA_STREAM_F2 != 0;
+#ifndef PASTA_SHFL_CONST
+#define PASTA_SHFL_CONST 1
+#endif
+constexpr bool kShflConst = PASTA_SHFL_CONST != 0;
 
 template <int VEC> __device__ __forceinline__ void v_scale(float (&y)[VEC], float a, const float (&x)[VEC]) {
     if constexpr (kF2 && VEC % 2 == 0) {
@@ -215,6 +219,7 @@ struct Ctx {
     uint64_t t0;
     uint64_t pol_rows;  // L2 evict-last policy for factor rows
     float g_scale;
+    bool sq_lane;       // this lane adds the squared residuals (loss fwd, or bwd with partials)
 };
 
 // Close the open run: a run continuing one of the previous tile (only the
@@ -240,6 +245,7 @@ __device__ __forceinline__ void close_run(const Ctx<T, N, KIND> &c,
 // R0L (loss kinds): 0 = position 0's row, needed where a run starts, is
 // gathered with the others in phase A (a register row per entry); 1 = it is
 // loaded in phase B when the run changes (fewer registers, a dependent load).
+
 // One batch's staged inputs between its two phases: position 0's indices and
 // the values of the four entries, and the rows gathered in phase A.
 template <int N, int NR>
@@ -279,7 +285,11 @@ __device__ __forceinline__ void batch_load(const Ctx<T, N, KIND> &c, uint32_t pr
     for (int q = 0; q < 4; ++q) {
         b.i0[q] = iw[0][q];
         const bool ok = !CHECK || q < lim;
-        b.need0[q] = ok && iw[0][q] != (q == 0 ? prev0 : iw[0][q - 1]);
+        // Only R0L = 0 loads position 0 here.  R0L = 1 tests the run change
+        // in phase B, where it is the same test (the entries of a batch are
+        // in stream order and invalid ones only trail it); not carrying the
+        // flags across the phases made the loss pass 1-6% faster.
+        if (P0 == 0) b.need0[q] = ok && iw[0][q] != (q == 0 ? prev0 : iw[0][q - 1]);
 #pragma unroll
         for (int p = P0; p < N; ++p) {
             const uint4 *ptr = reinterpret_cast<const uint4 *>(c.ub[p] + (uint64_t)iw[p][q] * c.stride);
@@ -298,7 +308,7 @@ __device__ __forceinline__ void batch_load(const Ctx<T, N, KIND> &c, uint32_t pr
 // R0L (loss kinds): 0 = position 0's row, needed where a run starts, was
 // gathered in phase A (a register row per entry); 1 = it is loaded here when
 // the run changes (fewer registers, a dependent load).
-template <bool CHECK, int R0L, typename T, int N, int KIND>
+template <bool CHECK, int R0L, int LC, typename T, int N, int KIND>
 __device__ __forceinline__ void batch_compute(const Ctx<T, N, KIND> &c, GroupState<Ctx<T, N, KIND>::VEC> &s,
                                               const Staged<N, Shape<N, KIND, R0L>::NR> &b, int lim,
                                               uint64_t pos) {
@@ -321,7 +331,9 @@ __device__ __forceinline__ void batch_compute(const Ctx<T, N, KIND> &c, GroupSta
         }
         if (changed) s.cur = b.i0[q];
         if constexpr (!MT && R0L) {
-            if (b.need0[q])
+            // the run's row where it starts (a divergent branch measured faster
+            // than a predicated load on every lane group)
+            if (changed)
                 s.row0 = ld_row(reinterpret_cast<const uint4 *>(c.ub[0] + (uint64_t)b.i0[q] * c.stride),
                                 c.pol_rows);
         } else if (!MT && b.need0[q]) {
@@ -360,7 +372,12 @@ __device__ __forceinline__ void batch_compute(const Ctx<T, N, KIND> &c, GroupSta
             }
             widen<T, VEC>(s.row0, r);
             float part = v_dot<VEC>(p, r);
-            for (int o = c.L >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o, c.L);
+            if constexpr (LC > 0 && kShflConst) {  // the lane count compiled in: an unrolled tree
+#pragma unroll
+                for (int o = LC >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o, LC);
+            } else {
+                for (int o = c.L >> 1; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o, c.L);
+            }
             const float e_m = b.v[q] - part;
             if (KIND == kLossFwd) {
                 if (ok && c.lig == 0) {
@@ -373,7 +390,7 @@ __device__ __forceinline__ void batch_compute(const Ctx<T, N, KIND> &c, GroupSta
             } else if (ok) {
                 // fused forward: the backward pass over the first copy also
                 // sums the squared residuals (Args::partials set)
-                if (c.a.partials && c.lig == 0) s.sq32 = fmaf(e_m, e_m, s.sq32);
+                if (c.sq_lane) s.sq32 = fmaf(e_m, e_m, s.sq32);
                 const float w = -c.g_scale * e_m;
                 v_fma_s<VEC>(s.acc, w, p);
             }
@@ -382,12 +399,12 @@ __device__ __forceinline__ void batch_compute(const Ctx<T, N, KIND> &c, GroupSta
 }
 
 // One batch, both phases.
-template <bool CHECK, int R0L, typename T, int N, int KIND>
+template <bool CHECK, int R0L, int LC, typename T, int N, int KIND>
 __device__ __forceinline__ void batch(const Ctx<T, N, KIND> &c, GroupState<Ctx<T, N, KIND>::VEC> &s,
                                       const uint32_t *sb, int AS, int src, int lim, uint64_t pos) {
     Staged<N, Shape<N, KIND, R0L>::NR> b;
     batch_load<CHECK, R0L>(c, s.cur, sb, AS, src, lim, b);
-    batch_compute<CHECK, R0L>(c, s, b, lim, pos);
+    batch_compute<CHECK, R0L, LC>(c, s, b, lim, pos);
 }
 
 // LC: lanes per entry fixed at compile time (0 = read from Args), which turns
@@ -428,6 +445,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
                (size_t)(sidx % G) * a.R;
     };
     c.g_scale = (KIND == kLossBwd && a.gscale) ? (float)*a.gscale : 1.f;
+    c.sq_lane = lig == 0 && (KIND == kLossFwd || a.partials != nullptr);
 
     GroupState<VEC> s;
 #pragma unroll
@@ -477,10 +495,10 @@ __global__ void __launch_bounds__(kThreads, MINB) k_stream(const Args<T, N> a) {
             const uint64_t pos = t0 + (uint64_t)(i * chunk);
             if (__all_sync(kFull, rem >= chunk)) {
                 for (int src = 0; src < L; ++src)
-                    batch<false, R0L>(c, s, sb, AS, src, 4, pos + 4u * (uint64_t)src);
+                    batch<false, R0L, LC>(c, s, sb, AS, src, 4, pos + 4u * (uint64_t)src);
             } else {
                 for (int src = 0; src < L; ++src)
-                    batch<true, R0L>(c, s, sb, AS, src, rem - 4 * src, pos + 4u * (uint64_t)src);
+                    batch<true, R0L, LC>(c, s, sb, AS, src, rem - 4 * src, pos + 4u * (uint64_t)src);
             }
             if (KIND == kLossFwd || (KIND == kLossBwd && a.partials)) {
                 s.sq += (double)s.sq32;

@@ -119,7 +119,10 @@ pasta_status run(const StreamLaunch &l, cudaStream_t s) {
 // measurable and keeps one instantiation per type and order.
 template <typename T, int N, int KIND>
 pasta_status by_lanes(const StreamLaunch &l, cudaStream_t s) {
-    if constexpr (KIND == stream::kMttkrp || KIND == stream::kGather) {
+#ifndef PASTA_MTTKRP_LC
+#define PASTA_MTTKRP_LC 0
+#endif
+    if constexpr (KIND == stream::kGather || (KIND == stream::kMttkrp && !PASTA_MTTKRP_LC)) {
         return run<T, N, KIND, 0>(l, s);
     } else {
         switch (l.R * (int)sizeof(T) / 16) {
