@@ -63,6 +63,9 @@ def parse():
                          "zipf4d and zipf5d)")
     ap.add_argument("--no-multicore", action="store_true",
                     help="skip the multicore CPU baseline (privatized OpenMP MTTKRP)")
+    ap.add_argument("--hicoo", action="store_true",
+                    help="also time the HiCOO copy's build and MTTKRP against the sorted-copy MTTKRP "
+                         "(zipf3d, zipf4d, zipf5d; block sizes 2^7 and 2^8)")
     return ap.parse_args()
 
 
@@ -378,6 +381,8 @@ def run_own(args, rank, world, local):
     torch.cuda.empty_cache()
     if rank == 0 and not args.no_multicore and not args.no_cpu_baseline and not args.nnz:
         result["cpu_multicore"] = cpu_multicore(wl, args)
+    if args.hicoo and rank == 0:
+        result["hicoo"] = {name: hicoo_leg(pasta, synth, name, args, dev) for name in ("zipf3d", "zipf4d", "zipf5d")}
     if not args.no_legs and rank == 0 and not args.nnz:
         result["workloads"] = {name: workload_leg(pasta, synth, name, dts, peak, args, dev, loss)
                                for name, dts, loss in (("zipf4d", ("f32", "bf16"), False),
@@ -530,6 +535,45 @@ def workload_leg(pasta, synth, name, dts, peak, args, dev, with_loss):
         out[dt] = leg
         del Us, Ms
     X.close()
+    torch.cuda.empty_cache()
+    return out
+
+
+def hicoo_leg(pasta, synth, name, args, dev):
+    """HiCOO (row f3): build time, block count and MTTKRP per mode from the
+    HiCOO copy, next to the sorted-copy MTTKRP on the same tensor and FP32
+    factors, with the relative difference of their outputs."""
+    import torch
+    wl = synth.WORKLOADS[name]
+    if args.nnz:
+        wl = wl.scaled(nnz=int(args.nnz))
+    Xd = synth.generate(wl, device=dev)
+    Us = [u.contiguous() for u in synth.factors_for(wl, device=dev)]
+    X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
+    del Xd
+    X.sort_all()
+    out = {"workload": workload_desc(wl)}
+    K = max(3, args.steps // 6)
+    for bits in (7, 8):
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        nb = pasta.hicoo(X, bits)
+        b.record()
+        torch.cuda.synchronize()
+        res = {"nblocks": nb, "build_ms": round(a.elapsed_time(b), 2), "sorted_ms_per_mode": [],
+               "hicoo_ms_per_mode": [], "rel_diff_per_mode": []}
+        for n in range(wl.order):
+            M = pasta.mttkrp(X, Us, n)
+            H = pasta.hicoo_mttkrp(X, Us, n)
+            res["rel_diff_per_mode"].append(float((H.double() - M.double()).norm() / M.double().norm()))
+            res["sorted_ms_per_mode"].append(round(_time_ms(lambda: pasta.mttkrp(X, Us, n, out=M), K), 4))
+            res["hicoo_ms_per_mode"].append(round(_time_ms(lambda: pasta.hicoo_mttkrp(X, Us, n, out=H), K), 4))
+            del M, H
+        out[f"b{bits}"] = res
+    X.close()
+    del Us
     torch.cuda.empty_cache()
     return out
 

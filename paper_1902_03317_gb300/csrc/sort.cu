@@ -195,11 +195,8 @@ __device__ __forceinline__ uint32_t block_exclusive(uint32_t x, uint32_t *wsum) 
 // that order: consecutive threads write consecutive positions of one digit's
 // output range, so the writes coalesce.  Thread t owns digits t * PER ...
 // t * PER + PER - 1 in the per-digit steps.
-#ifndef PASTA_SCATTER_MINB
-#define PASTA_SCATTER_MINB 2
-#endif
 template <int BINS>
-__global__ void __launch_bounds__(kThreads, PASTA_SCATTER_MINB)
+__global__ void __launch_bounds__(kThreads, 2)
     k_scatter(const uint64_t *kin, const uint32_t *vin, uint64_t *kout, uint32_t *vout,
               uint64_t n, int shift, uint32_t mask, uint32_t ntiles, const uint32_t *hist,
               const uint32_t *totals) {

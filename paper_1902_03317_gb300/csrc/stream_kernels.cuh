@@ -111,6 +111,10 @@ constexpr bool kF2 = PASTA_STREAM_F2 != 0;
 #define PASTA_SHFL_CONST 1
 #endif
 constexpr bool kShflConst = PASTA_SHFL_CONST != 0;
+#ifndef PASTA_FAST_BATCH
+#define PASTA_FAST_BATCH 1
+#endif
+constexpr bool kFastBatch = PASTA_FAST_BATCH != 0;
 
 template <int VEC> __device__ __forceinline__ void v_scale(float (&y)[VEC], float a, const float (&x)[VEC]) {
     if constexpr (kF2 && VEC % 2 == 0) {
@@ -316,29 +320,8 @@ __device__ __forceinline__ void batch_compute(const Ctx<T, N, KIND> &c, GroupSta
     constexpr bool MT = Shape<N, KIND, R0L>::MT;
     constexpr int P0 = Shape<N, KIND, R0L>::P0;
     constexpr int NR = Shape<N, KIND, R0L>::NR;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const bool ok = !CHECK || q < lim;
-        const bool changed = ok && b.i0[q] != s.cur;
-        if (KIND != kLossFwd && KIND != kGather) {
-            if (__any_sync(kFull, changed)) {
-                if (changed) {
-                    if (s.cur != kNoRow) close_run(c, s);
-#pragma unroll
-                    for (int e = 0; e < VEC; ++e) s.acc[e] = 0.f;
-                }
-            }
-        }
-        if (changed) s.cur = b.i0[q];
-        if constexpr (!MT && R0L) {
-            // the run's row where it starts (a divergent branch measured faster
-            // than a predicated load on every lane group)
-            if (changed)
-                s.row0 = ld_row(reinterpret_cast<const uint4 *>(c.ub[0] + (uint64_t)b.i0[q] * c.stride),
-                                c.pol_rows);
-        } else if (!MT && b.need0[q]) {
-            s.row0 = b.rows[q][0];
-        }
+    // The arithmetic of entry q with the run state as it stands.
+    auto math = [&](int q, bool ok) {
         float p[VEC], r[VEC];
         if constexpr (KIND == kGather) {
 #pragma unroll
@@ -395,6 +378,49 @@ __device__ __forceinline__ void batch_compute(const Ctx<T, N, KIND> &c, GroupSta
                 v_fma_s<VEC>(s.acc, w, p);
             }
         }
+    };
+    if constexpr (KIND == kGather) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) math(q, !CHECK || q < lim);
+        return;
+    }
+    if constexpr (kFastBatch) {
+        // No lane group of the warp starts a run in this batch (the common
+        // case on long runs): one vote instead of one per entry.
+        bool any = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            any |= (!CHECK || q < lim) && b.i0[q] != (q == 0 ? s.cur : b.i0[q - 1]);
+        if (!__any_sync(kFull, any)) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) math(q, !CHECK || q < lim);
+            return;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const bool ok = !CHECK || q < lim;
+        const bool changed = ok && b.i0[q] != s.cur;
+        if (KIND != kLossFwd) {
+            if (__any_sync(kFull, changed)) {
+                if (changed) {
+                    if (s.cur != kNoRow) close_run(c, s);
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) s.acc[e] = 0.f;
+                }
+            }
+        }
+        if (changed) s.cur = b.i0[q];
+        if constexpr (!MT && R0L) {
+            // the run's row where it starts (a divergent branch measured faster
+            // than a predicated load on every lane group)
+            if (changed)
+                s.row0 = ld_row(reinterpret_cast<const uint4 *>(c.ub[0] + (uint64_t)b.i0[q] * c.stride),
+                                c.pol_rows);
+        } else if (!MT && b.need0[q]) {
+            s.row0 = b.rows[q][0];
+        }
+        math(q, ok);
     }
 }
 

@@ -64,7 +64,6 @@ constexpr int row0_late() {
 // L); LC = 0 reads it from the arguments.
 template <typename T, int N, int KIND, int LC>
 pasta_status run(const StreamLaunch &l, cudaStream_t s) {
-    static_assert(KIND != stream::kGather || LC == 0, "the gather kind takes its lane count at run time");
     constexpr int MINB = min_blocks<T, N, KIND>();
     Args<T, N> a{};
     for (int p = 0; p < N; ++p) {
@@ -112,19 +111,14 @@ pasta_status run(const StreamLaunch &l, cudaStream_t s) {
     return PASTA_OK;
 }
 
-// The loss kinds get a compiled-in lane count for the common row widths
-// (32..256 bytes: R = 8..64 in FP32, 16..128 in 16-bit); it turns the lane
-// group's strides, shared-memory offsets and shuffle widths into constants,
-// which measured 4-6% faster for the backward.  MTTKRP gained nothing
-// measurable and keeps one instantiation per type and order.
+// MTTKRP and the loss kinds get a compiled-in lane count for the common row
+// widths (32..256 bytes: R = 8..64 in FP32, 16..128 in 16-bit); it turns the
+// lane group's strides, shared-memory offsets and shuffle widths into
+// constants and unrolls the chunk's batches (loss passes 4-6% faster, MTTKRP
+// 0.2-1.2%).  The gather probe is compiled the same way as MTTKRP.
 template <typename T, int N, int KIND>
 pasta_status by_lanes(const StreamLaunch &l, cudaStream_t s) {
-#ifndef PASTA_MTTKRP_LC
-#define PASTA_MTTKRP_LC 0
-#endif
-    if constexpr (KIND == stream::kGather || (KIND == stream::kMttkrp && !PASTA_MTTKRP_LC)) {
-        return run<T, N, KIND, 0>(l, s);
-    } else {
+    {
         switch (l.R * (int)sizeof(T) / 16) {
             case 2: return run<T, N, KIND, 2>(l, s);
             case 4: return run<T, N, KIND, 4>(l, s);
