@@ -91,3 +91,36 @@ def test_noalloc_rejects_bad_sizes_and_alignment():
     mis = _lib.ptr_array([idx[0].data_ptr(), idx[1].data_ptr() + 4, idx[2].data_ptr()])
     assert call(ip=mis) == "PASTA_ERR_ALIGNMENT"
     torch.cuda.synchronize()
+
+
+def test_noalloc_call_allocates_nothing():
+    """After the first call on the device (which looks up the scratch array's
+    address), further calls change neither the device's free memory nor the
+    allocation count of torch's caching allocator (which the library's own
+    buffers would go through)."""
+    nnz, dims, R = 50_000, (5_000, 3_000, 1_000), 32
+    Xh = synth.generate(G.small("zipf3d", nnz, dims))
+    _, Us, _ = G.factors(dims, R, 23)
+    idx = [_padded(i.to(G.DEV)) for i in Xh.idx]
+    val = _padded(Xh.val.to(G.DEV))
+    loss = torch.zeros((), dtype=torch.float64, device=G.DEV)
+    e = torch.zeros(nnz, dtype=torch.float32, device=G.DEV)
+    lib = _lib.lib()
+
+    def call():
+        st = lib.pasta_cp_loss_fwd_noalloc(
+            3, _lib.u64_array(dims), nnz, _lib.ptr_array([t.data_ptr() for t in idx]), val.data_ptr(),
+            _lib.ptr_array([u.data_ptr() for u in Us]), 0, R, loss.data_ptr(), e.data_ptr(),
+            torch.cuda.current_stream().cuda_stream)
+        _lib.check(st, "pasta_cp_loss_fwd_noalloc")
+
+    call()
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    n0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    for _ in range(3):
+        call()
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == n0
