@@ -223,23 +223,13 @@ def run_own(args, rank, world, local):
         wl = wl.scaled(nnz=int(args.nnz))
     N = wl.order
     # ---- inputs, resident in HBM
-    Xd = synth.generate(wl, device=dev)
+    Xd = synth.generate(wl, device=dev, model_values=planted_model_values)
     fdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[args.factor_dtype]
     Us = [u.to(fdt).contiguous() for u in synth.factors_for(wl, device=dev)]
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     # rows of each factor touched (algorithmic bytes), counted before timing
     touched = [int(torch.unique(ix).numel()) for ix in Xd.idx]
-    t_sort = []
-    for n in range(N):
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        X.sort_by_mode(n)
-        e1.record()
-        torch.cuda.synchronize()
-        t_sort.append(e0.elapsed_time(e1))
-    X.sort_by_mode(0)
+    t_sort = timed_sorts(X, N)
     Ms = [torch.empty((wl.dims[n], wl.R), device=dev) for n in range(N)]
     stream = torch.cuda.current_stream()
     # With several ranks the tensor is split, not replicated: rank r takes
@@ -475,6 +465,8 @@ def bf16_leg(pasta, X, wl, touched, peak, args, dev):
     Ub = [u.to(torch.bfloat16).contiguous() for u in synth.factors_for(wl, device=dev)]
     K = max(5, args.steps // 2)
     ms = [_time_ms(lambda: pasta.mttkrp(X, Ub, n), K) for n in range(N)]
+    sink = torch.empty(1 << 22, dtype=torch.float32, device=dev)
+    probe = [_time_ms(lambda: pasta.gather_probe(X, Ub, n, sink=sink), K) for n in range(N)]
     loss_ms = _time_ms(lambda: pasta.cp_loss_fwd_bwd(X, Ub), K)
     alg = [mttkrp_alg_bytes(wl.nnz, N, wl.R, 2, touched, wl.dims, n) for n in range(N)]
     gbs = sum(alg) / (sum(ms) * 1e-3) / 1e9
@@ -482,6 +474,8 @@ def bf16_leg(pasta, X, wl, touched, peak, args, dev):
             for n in range(N)]
     lgbs = sum(lalg) / (loss_ms * 1e-3) / 1e9
     return {"mttkrp_ms_per_mode": [round(x, 4) for x in ms], "value_nnz_per_s": N * wl.nnz / (sum(ms) * 1e-3),
+            "gather_probe_ms_per_mode": [round(x, 4) for x in probe],
+            "mttkrp_over_probe": [round(a / b, 3) for a, b in zip(ms, probe)],
             "mttkrp_alg_bytes_per_mode": alg, "mttkrp_achieved_gbs": round(gbs, 1),
             "mttkrp_frac": round(gbs / peak, 4), "loss_fwd_bwd_ms": round(loss_ms, 4),
             "loss_achieved_gbs": round(lgbs, 1), "loss_frac": round(lgbs / peak, 4)}
@@ -496,21 +490,12 @@ def workload_leg(pasta, synth, name, dts, peak, args, dev, with_loss):
     import torch
     wl = synth.WORKLOADS[name]
     N = wl.order
-    Xd = synth.generate(wl, device=dev)
+    Xd = synth.generate(wl, device=dev, model_values=planted_model_values)
     touched = [int(torch.unique(ix).numel()) for ix in Xd.idx]
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     del Xd
     torch.cuda.empty_cache()
-    t_sort = []
-    for n in range(N):
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        X.sort_by_mode(n)
-        b.record()
-        torch.cuda.synchronize()
-        t_sort.append(round(a.elapsed_time(b), 3))
+    t_sort = [round(x, 3) for x in timed_sorts(X, N)]
     out = {"workload": workload_desc(wl), "sort_ms_per_mode": t_sort}
     K = max(5, args.steps // 3)
     for dt in dts:
@@ -547,7 +532,7 @@ def hicoo_leg(pasta, synth, name, args, dev):
     wl = synth.WORKLOADS[name]
     if args.nnz:
         wl = wl.scaled(nnz=int(args.nnz))
-    Xd = synth.generate(wl, device=dev)
+    Xd = synth.generate(wl, device=dev, model_values=planted_model_values)
     Us = [u.contiguous() for u in synth.factors_for(wl, device=dev)]
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     del Xd
@@ -578,6 +563,24 @@ def hicoo_leg(pasta, synth, name, args, dev):
     return out
 
 
+def timed_sorts(X, N):
+    """Sort every mode in the order sort_all uses (0, N-1, ..., 1: each copy
+    after the first re-sorted from the next mode's copy on its own field),
+    each timed with CUDA events; returns ms indexed by mode."""
+    import torch
+    t = [0.0] * N
+    for n in [0] + list(range(N - 1, 0, -1)):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        X.sort_by_mode(n)
+        e1.record()
+        torch.cuda.synchronize()
+        t[n] = e0.elapsed_time(e1)
+    return t
+
+
 def sort_roofline(t_sort, nnz, N, peak):
     """Mode sorts (preprocessing, timed once per mode with CUDA events; the
     first includes growing the handle's scratch buffer).  Compulsory bytes per
@@ -590,8 +593,8 @@ def sort_roofline(t_sort, nnz, N, peak):
     return {"sort_ms_per_mode": [round(x, 2) for x in t_sort], "alg_bytes_per_mode": alg,
             "achieved_gbs": round(achieved, 1), "frac": round(achieved / peak, 4),
             "note": ("LSD radix passes of up to 9-bit digits over (64-bit key, 32-bit value) pairs, 24 bytes "
-                     "per entry per pass; the first mode from the creation-order copy, later modes from the "
-                     "previous mode's copy on the remaining key fields")}
+                     "per entry per pass; mode 0 from the creation-order copy, then modes N-1, ..., 1, each "
+                     "from the next mode's copy on its own index field only")}
 
 
 def als_timing(pasta, X, Us, wl, args, mttkrp_ms):
@@ -701,11 +704,31 @@ def ttm_timing(pasta, X, wl, peak, args):
     return out
 
 
+def planted_model_values(coords, planted):
+    """Values of the planted-model workload before noise: the CP model
+    sum_r prod_k A_k(i_k, r) at every coordinate, FP64, in chunks on the
+    coordinates' device (input preparation; the tests make the same values
+    with the oracle's evaluator)."""
+    import torch
+    dev = coords[0].device
+    n = coords[0].numel()
+    A64 = [A.to(device=dev, dtype=torch.float64) for A in planted]
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    step = 1 << 22
+    for lo in range(0, n, step):
+        acc = None
+        for c, A in zip(coords, A64):
+            rows = A[c[lo:lo + step].long()]
+            acc = rows if acc is None else acc * rows
+        out[lo:lo + step] = acc.sum(dim=1)
+    return out
+
+
 def loss_compare(pasta, synth, dev, args):
     """CP-loss forward+backward time, FP32 vs BF16 factors (cploss3d)."""
     import torch
     wl = synth.WORKLOADS[LOSS_WORKLOAD]
-    Xd = synth.generate(wl, device=dev)
+    Xd = synth.generate(wl, device=dev, model_values=planted_model_values)
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     X.sort_by_mode(0)
     del Xd
@@ -743,7 +766,7 @@ def e2e(pasta, synth, wl, dev, args, world):
     copies the COO tensor and factors in, builds the handle and sorted
     copies, runs the MTTKRP sweep and reads every output back."""
     import torch
-    Xh = synth.generate(wl, device=dev)
+    Xh = synth.generate(wl, device=dev, model_values=planted_model_values)
     idx_h = [i.cpu().pin_memory() for i in Xh.idx]
     val_h = Xh.val.cpu().pin_memory()
     Uh = [u.cpu().pin_memory() for u in synth.factors_for(wl, device=dev)]
@@ -754,15 +777,43 @@ def e2e(pasta, synth, wl, dev, args, world):
     h2d = sum(t.numel() * t.element_size() for t in idx_h + [val_h] + Uh)
     d2h = sum(t.numel() * t.element_size() for t in outs)
 
+    # Streams: `side` carries the factor upload (overlapping the create and
+    # the first sort) and each output's download (overlapping later work);
+    # `aux` sorts modes 1..N-1 (each derived from the previous mode's copy)
+    # while the main stream runs the MTTKRPs of the modes already sorted.
+    # Sorts share the handle's scratch buffer, so they stay on one stream;
+    # MTTKRP n waits for sort n's event.
+    side = torch.cuda.Stream(device=dev)
+    aux = torch.cuda.Stream(device=dev)
+    main = torch.cuda.current_stream(dev)
+
     def one():
         idx = [t.to(dev, non_blocking=True) for t in idx_h]
         val = val_h.to(dev, non_blocking=True)
-        Us = [u.to(dev, non_blocking=True) for u in Uh]
+        side.wait_stream(main)
+        with torch.cuda.stream(side):
+            Us = [u.to(dev, non_blocking=True) for u in Uh]
         X = pasta.CooTensor(wl.dims, idx, val, validate=False)
         del idx, val
-        for n in range(N):
+        X.sort_by_mode(0)
+        aux.wait_stream(main)
+        sorted_ev = [None]
+        with torch.cuda.stream(aux):
+            for n in range(N - 1, 0, -1):  # each from the next mode's copy (see sort_all)
+                X.sort_by_mode(n)
+                sorted_ev.append(aux.record_event())
+        main.wait_stream(side)
+        for u in Us:
+            u.record_stream(main)
+        order = [0] + list(range(N - 1, 0, -1))  # modes in the order their copies appear
+        for i, n in enumerate(order):
+            if sorted_ev[i] is not None:
+                main.wait_event(sorted_ev[i])
             M = pasta.mttkrp(X, Us, n)
-            outs[n].copy_(M, non_blocking=True)
+            side.wait_stream(main)
+            with torch.cuda.stream(side):
+                outs[n].copy_(M, non_blocking=True)
+            M.record_stream(side)
         torch.cuda.synchronize()
         X.close()
 
@@ -821,7 +872,9 @@ def e2e(pasta, synth, wl, dev, args, world):
     return {"value": world * N * wl.nnz / dt, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": steps,
             "median_step_ms": sorted(per_step)[len(per_step) // 2],
-            "includes": "H2D of COO+factors, create, sort every mode, MTTKRP every mode, D2H of outputs",
+            "includes": ("H2D of COO+factors, create, sort every mode, MTTKRP every mode, D2H of outputs "
+                         "(factor upload and output downloads on a side stream; sorts of modes 1.. on a "
+                         "second stream, overlapping the MTTKRPs of the modes before)"),
             "breakdown_ms": br, "per_step_ms": per_step}
 
 
@@ -834,7 +887,7 @@ def oracle_sample(wl, sample: int):
     import torch
     from paper_1902_03317_gb300 import synth
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    Xd = synth.generate(wl, device=dev)
+    Xd = synth.generate(wl, device=dev, model_values=planted_model_values)
     n = min(sample, wl.nnz)
     idx = [i[:n].cpu().numpy().astype(np.uint32) for i in Xd.idx]
     val = Xd.val[:n].cpu().numpy().astype(np.float64)
@@ -879,7 +932,8 @@ def cpu_multicore(wl, args):
     import oracle
     from paper_1902_03317_gb300 import synth
     import torch
-    Xd = synth.generate(wl, device="cuda" if torch.cuda.is_available() else "cpu")
+    Xd = synth.generate(wl, device="cuda" if torch.cuda.is_available() else "cpu",
+                        model_values=planted_model_values)
     idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
     val = Xd.val.cpu().numpy()
     del Xd

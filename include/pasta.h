@@ -133,7 +133,12 @@ pasta_status pasta_coo_info(pasta_coo X, int *order, uint64_t *dims, uint64_t *n
  * creation-order entry perm[p]).  When the key holds every index (the modes'
  * bits fit 64), the sort carries the values and leaves perm to be built on
  * first request (pasta_coo_view with d_perm, pasta_coo_copy_out with
- * d_perm_out), which sorts again.  A second call for the same mode is a no-op.
+ * d_perm_out), which sorts again.  In that case the copy of mode+1, when it
+ * exists, is only re-sorted on the mode-`mode` field (it is ordered by the
+ * other fields already), else the copy of mode-1 on every field but mode-1's;
+ * so sorting the modes in the order 0, N-1, N-2, ..., 1 (pasta's Python
+ * sort_all) costs the least.  The result is the same whichever copies exist.
+ * A second call for the same mode is a no-op.
  * Temporary device memory (about 21 bytes per entry) is the handle's scratch
  * buffer: allocated on first use (cudaMalloc, which waits for the device),
  * reused by later sorts and CP-ALS sweeps on the handle, grown when a call

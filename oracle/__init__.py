@@ -128,6 +128,7 @@ def _load():
                                    ctypes.c_int, P, P],
                 "oracle_cp_grad": [ctypes.c_int, P, ctypes.c_uint64, P, P, P,
                                    ctypes.c_int, ctypes.c_double, P],
+                "oracle_cp_model": [ctypes.c_int, ctypes.c_uint64, P, P, ctypes.c_int, P],
             }.items():
                 fn = getattr(lib, name)
                 fn.argtypes = argt
@@ -193,6 +194,33 @@ def cp_loss(dims, idx, val, U, want_resid: bool = False):
     if rc != 0:
         raise ValueError("oracle_cp_loss rejected its arguments")
     return (float(loss[0]), resid) if want_resid else float(loss[0])
+
+
+def cp_model_values(dims, idx, U) -> np.ndarray:
+    """CP model sum_r prod_k U_k(i_k(m), r) at every stored coordinate, FP64
+    (Sec. 2.2).  Tests also use it to make the values of the planted-model
+    workload: ``synth.generate(wl, model_values=...)`` takes this evaluator,
+    wrapped by ``planted_model``, since the shared generator holds none of
+    the method's arithmetic."""
+    R = int(np.asarray(U[0]).shape[1])
+    nnz = int(np.asarray(idx[0]).shape[0])
+    dims, order, nnz, idx, _, Ud, ip, up = _prep(dims, idx, np.zeros(nnz), U, R)
+    out = np.empty(nnz, dtype=np.float64)
+    rc = _load().oracle_cp_model(order, nnz, ip, up, R, _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_cp_model rejected its arguments")
+    return out
+
+
+def planted_model(coords, planted):
+    """``synth.generate``'s ``model_values`` hook backed by the oracle:
+    torch coordinates and planted factors in, FP64 torch values out on the
+    coordinates' device."""
+    import torch
+    dims = [int(p.shape[0]) for p in planted]
+    v = cp_model_values(dims, [c.cpu().numpy().astype(np.uint32) for c in coords],
+                        [p.cpu().double().numpy() for p in planted])
+    return torch.from_numpy(v).to(coords[0].device)
 
 
 def cp_grad(dims, idx, val, U, g: float = 1.0):

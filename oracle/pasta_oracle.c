@@ -82,6 +82,22 @@ static double cp_model_at(int order, const uint32_t *const *idx, uint64_t m,
 }
 
 /*
+ * CP model values at every stored coordinate, out[m] = model(m) (Sec. 2.2).
+ * Also makes the values of the planted-model test workload (the model's
+ * values plus noise); the generator that draws the coordinates does not
+ * evaluate the model itself.
+ */
+int oracle_cp_model(int order, uint64_t nnz, const uint32_t *const *idx,
+                    const double *const *U, int R, double *out)
+{
+    if (order < 1 || R < 1)
+        return -1;
+    for (uint64_t m = 0; m < nnz; ++m)
+        out[m] = cp_model_at(order, idx, m, U, R);
+    return 0;
+}
+
+/*
  * Sparse CP least-squares loss over the stored entries only:
  *     e(m) = val(m) - model(m),   L = 1/2 * sum_m e(m)^2.
  * The paper names gradient-descent CPD (Sec. 2.2) but prints no loss; this is

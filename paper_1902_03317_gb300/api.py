@@ -164,7 +164,10 @@ class CooTensor:
         return self
 
     def sort_all(self) -> "CooTensor":
-        for n in range(self.order):
+        """Build every mode's sorted copy, in the order 0, N-1, ..., 1: each
+        copy after the first is then sorted from the next mode's copy on its
+        own index field only."""
+        for n in [0] + list(range(self.order - 1, 0, -1)):
             self.sort_by_mode(n)
         return self
 

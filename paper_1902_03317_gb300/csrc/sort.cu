@@ -535,16 +535,28 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
     if (key_holds_all(gd, X->order)) {
         // the values travel as the payload and every index is decoded from
         // the sorted keys: nothing is gathered; the permutation is built on
-        // request (ensure_perm).  The key's least significant field is mode
-        // n-1; if the mode-(n-1) sorted copy exists it is already ordered by
-        // that field (it leads its own key), so a stable sort of it on the
-        // other fields alone gives the same order (ties in them keep the
-        // copy's order: by mode n-1, then creation order).
+        // request (ensure_perm).  A copy already sorted for a neighbouring
+        // mode saves passes, the stable sort keeping its order among ties:
+        //  - mode n+1's copy is ordered by (n+1, ..., n-1, n), which is mode
+        //    n's key without its leading field; a stable sort of it on the
+        //    mode-n field alone (the key's top bits) gives mode n's order;
+        //  - else mode n-1's copy is ordered by (n-1, n, ..., n-2); its
+        //    leading field is the least significant field of mode n's key,
+        //    so a stable sort on the other fields gives mode n's order.
+        // Ties in the sorted fields keep the copy's order, which is by the
+        // remaining fields and then creation order, as in the full sort.
+        const int next = (mode + 1) % X->order;
         const int prev = (mode + X->order - 1) % X->order;
-        const StoredCopy &pc = X->sorted[prev];
-        const bool derive = prev != mode && pc.present;
-        const int low = derive ? bits_for(X->dims[prev]) : 0;
-        pasta_status st = radix_sort(X, derive ? pc : X->orig, ks, low, used, true,
+        const StoredCopy *src = &X->orig;
+        int low = 0;
+        if (X->sorted[next].present) {
+            src = &X->sorted[next];
+            low = used - bits_for(X->dims[mode]);
+        } else if (X->sorted[prev].present) {
+            src = &X->sorted[prev];
+            low = bits_for(X->dims[prev]);
+        }
+        pasta_status st = radix_sort(X, *src, ks, low, used, true,
                                      reinterpret_cast<uint32_t *>(dst.val), &keys, s);
         if (st != PASTA_OK) return st;
         k_decode<<<gblocks, 256, 0, s>>>(keys, n, X->order, gd);

@@ -6,10 +6,11 @@ long-tailed mode sizes and power-law slice densities, generated from a seed.
 No record of any real dataset is reproduced.
 
 This module is shared by the CUDA path's tests and bench and by the oracle's
-tests, so it holds no MTTKRP or loss arithmetic: it only draws random
-coordinates, values and factors.  The one computed quantity is the planted CP
-model used to make the values of the loss workload (a data recipe, never an
-expected value).
+tests, so it holds none of the method's arithmetic: it only draws random
+coordinates, values and factors.  The planted-model workload's values are the
+CP model at the drawn coordinates plus noise; the caller passes the model
+evaluator in (``model_values``): the tests pass the oracle's, ``bench.py`` its
+own, and this module only adds the noise.
 
 Workloads (the five shapes the build measures and tests on):
 
@@ -38,7 +39,7 @@ from __future__ import annotations
 
 import dataclasses
 import math
-from typing import Sequence
+from typing import Callable, Sequence
 
 import torch
 
@@ -100,10 +101,11 @@ class _ZipfSampler:
     """Bounded Zipf(s) over ranks 1..dim mapped through a random permutation."""
 
     def __init__(self, dim: int, s: float, device, g: torch.Generator):
-        k = torch.arange(1, dim + 1, device=device, dtype=torch.float64)
-        w = k.pow(-float(s))
-        cdf = torch.cumsum(w, 0)
-        self.cdf = cdf / cdf[-1]
+        # the CDF is summed on the host (a sequential FP64 sum), so that the
+        # same seed gives the same tensor on any device and in every run
+        k = torch.arange(1, dim + 1, dtype=torch.float64)
+        cdf = torch.cumsum(k.pow(-float(s)), 0)
+        self.cdf = (cdf / cdf[-1]).to(device)
         self.perm = torch.randperm(dim, device=device, generator=g).to(torch.int32)
         self.dim = dim
 
@@ -175,20 +177,16 @@ def generate_factors(dims: Sequence[int], R: int, device="cpu", seed: int = 0,
             for d in dims]
 
 
-def planted_values(coords: list[torch.Tensor], planted: list[torch.Tensor]) -> torch.Tensor:
-    """Values of the planted CP model at the coordinates (data recipe for the
-    loss workload): sum over the planted rank of the product of the gathered
-    factor entries, in FP64, returned as FP32."""
-    acc = None
-    for c, A in zip(coords, planted):
-        rows = A.to(torch.float64)[c.long()]
-        acc = rows if acc is None else acc * rows
-    return acc.sum(dim=1).to(torch.float32)
+ModelValues = Callable[[list[torch.Tensor], list[torch.Tensor]], torch.Tensor]
 
 
 def generate_values(wl: Workload, coords: list[torch.Tensor], device="cpu",
-                    seed: int | None = None) -> tuple[torch.Tensor, list[torch.Tensor] | None]:
-    """Values for ``coords``.  Returns (values, planted factors or None)."""
+                    seed: int | None = None, model_values: ModelValues | None = None
+                    ) -> tuple[torch.Tensor, list[torch.Tensor] | None]:
+    """Values for ``coords``.  Returns (values, planted factors or None).
+
+    A "planted" workload needs ``model_values(coords, planted)``: the CP
+    model's value at every coordinate (FP64 or FP32, on ``device``)."""
     seed = (wl.seed if seed is None else seed) + 1000
     g = _gen(device, seed)
     n = coords[0].numel()
@@ -200,8 +198,10 @@ def generate_values(wl: Workload, coords: list[torch.Tensor], device="cpu",
         return torch.exp(torch.randn(n, device=device, generator=g)), None
     if wl.values == "planted":
         planted = generate_factors(wl.dims, wl.planted_R, device=device, seed=seed + 1)
-        v = planted_values(coords, planted)
-        v = v + wl.noise_sigma * torch.randn(n, device=device, generator=g)
+        if model_values is None:
+            raise ValueError(f"workload {wl.name!r} has planted-model values: pass model_values")
+        v = model_values(coords, planted).to(device=device, dtype=torch.float64)
+        v = (v + wl.noise_sigma * torch.randn(n, device=device, generator=g)).to(torch.float32)
         return v, planted
     raise ValueError(wl.values)
 
@@ -225,9 +225,10 @@ class Tensor:
                       None if self.planted is None else [p.to(device) for p in self.planted])
 
 
-def generate(wl: Workload, device="cpu", seed: int | None = None) -> Tensor:
+def generate(wl: Workload, device="cpu", seed: int | None = None,
+             model_values: ModelValues | None = None) -> Tensor:
     coords = generate_coords(wl, device=device, seed=seed)
-    val, planted = generate_values(wl, coords, device=device, seed=seed)
+    val, planted = generate_values(wl, coords, device=device, seed=seed, model_values=model_values)
     return Tensor(wl, tuple(wl.dims), coords, val.to(torch.float32).contiguous(), planted)
 
 

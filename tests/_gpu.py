@@ -41,3 +41,9 @@ def factors(dims, R, seed, dtype=torch.float32):
 
 def small(name, nnz, dims, seed=None, R=None):
     return synth.WORKLOADS[name].scaled(nnz=nnz, dims=dims, seed=seed, R=R)
+
+
+def generate(wl, **kw) -> synth.Tensor:
+    """``synth.generate`` with the oracle evaluating the planted CP model of
+    the planted-value workload (cploss3d)."""
+    return synth.generate(wl, model_values=oracle.planted_model, **kw)

@@ -37,7 +37,7 @@ def subset(idx, val, mode, rows, dim):
 
 def mttkrp_rows_check(name, dtypes, max_heavy=None):
     wl = synth.WORKLOADS[name]
-    Xd = synth.generate(wl, device=G.DEV)
+    Xd = G.generate(wl, device=G.DEV)
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     X.sort_all()
     idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
@@ -79,7 +79,7 @@ def test_zipf5d_200M_bf16():
 
 def test_cploss3d_20M_loss_and_grad():
     wl = synth.WORKLOADS["cploss3d"]
-    Xd = synth.generate(wl, device=G.DEV)
+    Xd = G.generate(wl, device=G.DEV)
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     X.sort_all()
     idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
@@ -113,7 +113,7 @@ def test_zipf3d_100M_als_sweep_normal_equations():
     column of every factor has unit norm, and since U_2 = 0 is a feasible
     update, 0 <= fit <= 1."""
     wl = synth.WORKLOADS["zipf3d"]
-    Xd = synth.generate(wl, device=G.DEV)
+    Xd = G.generate(wl, device=G.DEV)
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     idx = [i.cpu().numpy().astype(np.uint32) for i in Xd.idx]
     val = Xd.val.cpu().numpy().astype(np.float64)
@@ -140,7 +140,7 @@ def test_zipf3d_100M_tew_eq_and_ts_sampled():
     stored positions against the oracle (coordinates bit-exact, values within
     1 FP32 ulp; the multiplications exact)."""
     wl = synth.WORKLOADS["zipf3d"]
-    Xd = synth.generate(wl, device=G.DEV)
+    Xd = G.generate(wl, device=G.DEV)
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     del Xd
     Y = pasta.ts(X, "mul", -0.37)
@@ -169,7 +169,7 @@ def test_zipf3d_100M_ttm_sampled_fibers():
     distinct (i_2, i_0) pairs, and sampled fibers (the heaviest and random
     ones) against the oracle run on the entries of those fibers."""
     wl = synth.WORKLOADS["zipf3d"]
-    Xd = synth.generate(wl, device=G.DEV)
+    Xd = G.generate(wl, device=G.DEV)
     X = pasta.CooTensor(Xd.dims, Xd.idx, Xd.val)
     n = 1
     key = (Xd.idx[2].to(torch.int64) * wl.dims[0] + Xd.idx[0].to(torch.int64))

@@ -42,7 +42,7 @@ def _check_format(X, Xh, bits):
 
 @pytest.mark.parametrize("name,nnz,dims,R,bits", SHAPES)
 def test_format_matches_oracle(name, nnz, dims, R, bits):
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     X = G.to_device(Xh)
     _check_format(X, Xh, bits)
     X.close()
@@ -65,7 +65,7 @@ def test_format_with_key_cut_and_rebuild():
 @pytest.mark.parametrize("name,nnz,dims,R,bits", SHAPES)
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_mttkrp_matches_oracle(name, nnz, dims, R, bits, dtype):
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, val = G.host(Xh)
     master, dev, rounded = G.factors(dims, R, 51, dtype)
     X = G.to_device(Xh)
@@ -99,7 +99,7 @@ def test_small_and_ragged(nnz):
 
 
 def test_errors():
-    Xh = G.synth.generate(G.small("zipf3d", 2000, (100, 90, 80)))
+    Xh = G.generate(G.small("zipf3d", 2000, (100, 90, 80)))
     X = G.to_device(Xh)
     _, dev, _ = G.factors((100, 90, 80), 32, 53)
     with pytest.raises(pasta.PastaError) as e:
@@ -121,7 +121,7 @@ def test_errors():
 def test_rank_and_type_sweep(dtype, R):
     """The lane-group geometry from 1 lane per row (FP32 R = 4) to 32 (BF16
     R = 256), and FP16 factors."""
-    Xh = G.synth.generate(G.small("zipf4d", 30_000, (900, 800, 70, 20)))
+    Xh = G.generate(G.small("zipf4d", 30_000, (900, 800, 70, 20)))
     idx, val = G.host(Xh)
     master, dev, rounded = G.factors(Xh.dims, R, 55, dtype)
     X = G.to_device(Xh)

@@ -31,7 +31,7 @@ def _copy_order(X, mode, nnz):
 
 @pytest.mark.parametrize("name,nnz,dims,R", SHAPES)
 def test_loss_and_grad_fp32(name, nnz, dims, R):
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, val = G.host(Xh)
     master, dev, _ = G.factors(dims, R, 11)
     X = G.to_device(Xh)
@@ -53,7 +53,7 @@ def test_loss_and_grad_fp32(name, nnz, dims, R):
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
 @pytest.mark.parametrize("name,nnz,dims,R", [SHAPES[1], SHAPES[3], SHAPES[4]])
 def test_loss_and_grad_low_precision(name, nnz, dims, R, dtype):
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, val = G.host(Xh)
     master, dev, rounded = G.factors(dims, R, 12, dtype)
     X = G.to_device(Xh)
@@ -77,7 +77,7 @@ def test_loss_and_grad_low_precision(name, nnz, dims, R, dtype):
 
 
 def test_loss_is_bitwise_reproducible():
-    Xh = G.synth.generate(G.small("zipf3d", 200_000, (20_000, 10_000, 4_000)))
+    Xh = G.generate(G.small("zipf3d", 200_000, (20_000, 10_000, 4_000)))
     _, dev, _ = G.factors(Xh.dims, 32, 3)
     X = G.to_device(Xh)
     a = pasta.cp_loss_fwd(X, dev).item()
@@ -90,7 +90,7 @@ def test_planted_model_loss_is_noise_level():
     """Values = planted rank-16 model + N(0, 0.01^2); fitting with
     [planted | 0] (R = 32) leaves only the noise: loss ~ nnz * sigma^2 / 2."""
     wl = G.small("cploss3d", 200_000, (5_000, 5_000, 5_000))
-    Xh = G.synth.generate(wl)
+    Xh = G.generate(wl)
     idx, val = G.host(Xh)
     fit = [torch.cat([p, torch.zeros_like(p)], dim=1) for p in Xh.planted]
     X = G.to_device(Xh)
@@ -105,7 +105,7 @@ def test_planted_model_loss_is_noise_level():
 
 
 def test_autograd_function_matches_kernels_and_returns_param_dtype():
-    Xh = G.synth.generate(G.small("zipf4d", 50_000, (2000, 2000, 200, 50)))
+    Xh = G.generate(G.small("zipf4d", 50_000, (2000, 2000, 200, 50)))
     _, dev, _ = G.factors(Xh.dims, 32, 4, torch.bfloat16)
     X = G.to_device(Xh)
     X.sort_by_mode(1)
@@ -125,7 +125,7 @@ def test_gradcheck_fp64_30cube():
     """torch.autograd.gradcheck (FP64 finite differences) on a 30x30x30
     tensor with 500 entries, R = 32, through the FP64 kernels."""
     wl = G.small("cploss3d", 500, (30, 30, 30))
-    Xh = G.synth.generate(wl)
+    Xh = G.generate(wl)
     X = G.to_device(Xh)
     Us = [u.to(G.DEV) for u in G.synth.generate_factors(wl.dims, 32, seed=5, dtype=torch.float64)]
     Us = [u.requires_grad_(True) for u in Us]
@@ -141,7 +141,7 @@ def test_gradient_vs_oracle_finite_differences():
     """FP32 GPU gradient vs central differences of the FP64 oracle loss on a
     sample of entries (h = 1e-6)."""
     wl = G.small("cploss3d", 500, (30, 30, 30))
-    Xh = G.synth.generate(wl)
+    Xh = G.generate(wl)
     idx, val = G.host(Xh)
     master, dev, _ = G.factors(wl.dims, 32, 6)
     X = G.to_device(Xh)
@@ -174,7 +174,7 @@ def test_convert_rounds_to_nearest_even():
 @pytest.mark.parametrize("name,nnz,dims,R", [SHAPES[1], SHAPES[2], SHAPES[4]])
 def test_fused_loss_and_grad(name, nnz, dims, R, dtype):
     """pasta_cp_loss_fwd_bwd: the loss and all gradients in N passes."""
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, val = G.host(Xh)
     _, dev, rounded = G.factors(dims, R, 13, dtype)
     X = G.to_device(Xh)
@@ -192,7 +192,7 @@ def test_fused_loss_and_grad(name, nnz, dims, R, dtype):
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_autograd_per_mode_uses_fused_pass_and_scales(dtype):
-    Xh = G.synth.generate(G.small("zipf3d", 60_000, (5_000, 3_000, 1_000)))
+    Xh = G.generate(G.small("zipf3d", 60_000, (5_000, 3_000, 1_000)))
     idx, val = G.host(Xh)
     _, dev, rounded = G.factors(Xh.dims, 32, 14, dtype)
     X = G.to_device(Xh)

@@ -44,25 +44,25 @@ def check_all_modes(Xh, R, dtype, seed=7, tol=None):
 @pytest.mark.parametrize("name,nnz,dims,R", WORKLOADS)
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
 def test_workload_shapes(name, nnz, dims, R, dtype):
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     check_all_modes(Xh, R, dtype)
 
 
 @pytest.mark.parametrize("R", [1, 2, 3, 4, 5, 8, 12, 16, 17, 31, 32, 33, 48, 64, 100, 128, 200, 256])
 def test_rank_sweep_fp32(R):
-    Xh = G.synth.generate(G.small("zipf3d", 20_000, (3000, 2000, 1000)))
+    Xh = G.generate(G.small("zipf3d", 20_000, (3000, 2000, 1000)))
     check_all_modes(Xh, R, torch.float32)
 
 
 @pytest.mark.parametrize("R", [1, 3, 8, 16, 24, 40, 64, 256])
 def test_rank_sweep_bf16(R):
-    Xh = G.synth.generate(G.small("zipf4d", 20_000, (800, 800, 80, 20)))
+    Xh = G.generate(G.small("zipf4d", 20_000, (800, 800, 80, 20)))
     check_all_modes(Xh, R, torch.bfloat16)
 
 
 @pytest.mark.parametrize("R", [1, 2, 3, 32, 64, 256])
 def test_rank_sweep_fp64(R):
-    Xh = G.synth.generate(G.small("zipf3d", 10_000, (900, 500, 300)))
+    Xh = G.generate(G.small("zipf3d", 10_000, (900, 500, 300)))
     check_all_modes(Xh, R, torch.float64, tol=1e-12)
 
 
@@ -111,7 +111,7 @@ def test_untouched_rows_are_zero_and_output_overwritten():
 
 
 def test_misaligned_factors_take_the_scalar_path():
-    Xh = G.synth.generate(G.small("zipf3d", 30_000, (2000, 1000, 500)))
+    Xh = G.generate(G.small("zipf3d", 30_000, (2000, 1000, 500)))
     idx, val = G.host(Xh)
     master, _, _ = G.factors(Xh.dims, 8, 9)
     # factor views starting one element into their storage: not 16-byte aligned
@@ -128,7 +128,7 @@ def test_misaligned_factors_take_the_scalar_path():
 
 
 def test_mode_factor_is_not_read():
-    Xh = G.synth.generate(G.small("zipf3d", 10_000, (500, 400, 300)))
+    Xh = G.generate(G.small("zipf3d", 10_000, (500, 400, 300)))
     idx, val = G.host(Xh)
     master, dev, _ = G.factors(Xh.dims, 16, 2)
     X = G.to_device(Xh)
@@ -173,7 +173,7 @@ def test_error_statuses():
 
 
 def test_info_roundtrip():
-    Xh = G.synth.generate(G.small("zipf4d", 5000, (100, 90, 80, 7)))
+    Xh = G.generate(G.small("zipf4d", 5000, (100, 90, 80, 7)))
     X = G.to_device(Xh)
     order = ctypes.c_int()
     nnz = ctypes.c_uint64()

@@ -57,7 +57,7 @@ def _rounds_cap(nnz, R, dtype, cap):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_mttkrp_multi_round(name, nnz, dims, R, cap, dtype):
     cap = _rounds_cap(nnz, R, dtype, cap)
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, val = G.host(Xh)
     master, dev, rounded = G.factors(dims, R, 31, dtype)
     X = G.to_device(Xh)
@@ -75,7 +75,7 @@ def test_mttkrp_multi_round(name, nnz, dims, R, cap, dtype):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_loss_and_gradients_multi_round(name, nnz, dims, R, cap, dtype):
     cap = _rounds_cap(nnz, R, dtype, cap)
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, val = G.host(Xh)
     _, dev, rounded = G.factors(dims, R, 32, dtype)
     X = G.to_device(Xh)
@@ -108,7 +108,7 @@ def test_general_kernels_multi_round(dtype, R):
     """FP64 factors and R = 5 take the general (non-streaming) kernels, which
     stride over warp tiles the same way."""
     nnz, dims = 120_000, (3_000, 2_000, 1_000)
-    Xh = G.synth.generate(G.small("zipf3d", nnz, dims))
+    Xh = G.generate(G.small("zipf3d", nnz, dims))
     idx, val = G.host(Xh)
     master, dev, rounded = G.factors(dims, R, 33, dtype)
     X = G.to_device(Xh)
@@ -148,7 +148,7 @@ def test_zipf3d_16m_every_row():
     one block per SM (seven rounds)."""
     nnz = 16_000_000
     dims = (1_000_000, 500_000, 200_000)
-    Xh = G.synth.generate(G.small("zipf3d", nnz, dims), device=G.DEV).to("cpu")
+    Xh = G.generate(G.small("zipf3d", nnz, dims), device=G.DEV).to("cpu")
     idx, val = G.host(Xh)
     master, dev, _ = G.factors(dims, 32, 34)
     X = G.to_device(Xh)

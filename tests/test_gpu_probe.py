@@ -19,7 +19,7 @@ pytestmark = pytest.mark.gpu
     ("zipf5d", 150_000, (8, 50_000, 10_000, 1_000, 100), 16, torch.float32),
 ])
 def test_gather_probe_sums_the_gathered_rows(name, nnz, dims, R, dtype):
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, _ = G.host(Xh)
     _, dev, rounded = G.factors(dims, R, 41, dtype)
     X = G.to_device(Xh)
@@ -35,7 +35,7 @@ def test_gather_probe_sums_the_gathered_rows(name, nnz, dims, R, dtype):
 
 
 def test_gather_probe_rejects_uncovered_cases():
-    Xh = G.synth.generate(G.small("zipf3d", 1000, (50, 40, 30)))
+    Xh = G.generate(G.small("zipf3d", 1000, (50, 40, 30)))
     X = G.to_device(Xh)
     _, dev, _ = G.factors((50, 40, 30), 5, 1)  # R = 5: not a streaming case
     with pytest.raises(pasta.PastaError) as e:

@@ -24,7 +24,7 @@ pytestmark = pytest.mark.gpu
 ])
 @pytest.mark.parametrize("world", [1, 2, 3, 8])
 def test_ranges_sum_to_whole(name, nnz, dims, R, world):
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, val = G.host(Xh)
     master, dev, _ = G.factors(dims, R, 61)
     X = G.to_device(Xh)
@@ -52,7 +52,7 @@ def test_ranges_sum_to_whole(name, nnz, dims, R, world):
 
 
 def test_range_errors():
-    Xh = G.synth.generate(G.small("zipf3d", 1000, (100, 90, 80)))
+    Xh = G.generate(G.small("zipf3d", 1000, (100, 90, 80)))
     X = G.to_device(Xh)
     _, dev, _ = G.factors((100, 90, 80), 16, 62)
     with pytest.raises(pasta.PastaError) as e:

@@ -25,7 +25,7 @@ CASES = [
 
 @pytest.mark.parametrize("name,nnz,dims", CASES)
 def test_sorted_copies_match_oracle_exactly(name, nnz, dims):
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, val = G.host(Xh)
     X = G.to_device(Xh)
     for mode in range(len(dims)):
@@ -44,13 +44,14 @@ def test_sorted_copies_match_oracle_exactly(name, nnz, dims):
 
 @pytest.mark.parametrize("name,nnz,dims", CASES[:3])
 def test_sort_order_independent_of_which_copies_exist(name, nnz, dims):
-    """A mode's copy may be sorted from the previous mode's copy (already
-    ordered by the key's last field); the result must equal the sort from
-    the creation order whatever was sorted before."""
-    Xh = G.synth.generate(G.small(name, nnz, dims))
+    """A mode's copy may be sorted from the next mode's copy on its own field
+    alone, or from the previous mode's copy on the other fields; the result
+    must equal the sort from the creation order whatever was sorted before."""
+    Xh = G.generate(G.small(name, nnz, dims))
     idx, val = G.host(Xh)
     N = len(dims)
-    for sequence in (list(reversed(range(N))), [1, 0] + list(range(2, N))):
+    for sequence in (list(reversed(range(N))), [1, 0] + list(range(2, N)), [0] + list(range(N - 1, 0, -1)),
+                     [N - 1, 0] + list(range(1, N - 1))):
         X = G.to_device(Xh)
         for mode in sequence:
             X.sort_by_mode(mode)
@@ -68,7 +69,7 @@ def test_key_cut_to_64_bits_keeps_leading_modes_sorted():
     # 3 + 24 + 21 + 17 + 10 = 75 bits: the key holds modes 0,1,2 and the top
     # 16 bits of mode 3 when sorting for mode 0.
     dims = (8, 10_000_000, 2_000_000, 100_000, 1_000)
-    Xh = G.synth.generate(G.small("zipf5d", 30_000, dims))
+    Xh = G.generate(G.small("zipf5d", 30_000, dims))
     idx, _ = G.host(Xh)
     X = G.to_device(Xh)
     for mode in range(5):
@@ -106,3 +107,27 @@ def test_sort_small_and_ragged(nnz):
         _, _, perm = X.copy_out(mode)
         np.testing.assert_array_equal(perm.cpu().numpy().astype(np.int64), oracle.sort_perm(idx, mode))
     X.close()
+
+
+@pytest.mark.parametrize("dims", [(5, 1, 1), (1, 1, 1), (1, 6, 1, 3)])
+def test_sort_with_size_one_modes(dims):
+    """Modes of size 1 take no key bits; a copy derived from the previous
+    mode's copy can then have no bit left to sort (one pass of width 0)."""
+    nnz = 3000
+    g = torch.Generator().manual_seed(len(dims) + sum(dims))
+    Xh = G.synth.Tensor(None, dims, [torch.randint(0, d, (nnz,), generator=g, dtype=torch.int32) for d in dims],
+                        torch.rand(nnz, generator=g))
+    idx, val = G.host(Xh)
+    N = len(dims)
+    for sequence in (list(range(N)), list(reversed(range(N)))):
+        X = G.to_device(Xh)
+        for mode in sequence:
+            X.sort_by_mode(mode)
+        for mode in range(N):
+            sidx, sval, perm = X.copy_out(mode)
+            perm = perm.cpu().numpy().astype(np.int64)
+            np.testing.assert_array_equal(perm, oracle.sort_perm(idx, mode))
+            for k in range(N):
+                np.testing.assert_array_equal(sidx[k].cpu().numpy().astype(np.uint32), idx[k][perm])
+            np.testing.assert_array_equal(sval.cpu().numpy(), val[perm].astype(np.float32))
+        X.close()

@@ -186,6 +186,18 @@ def test_planted_exact_model_has_zero_loss_and_gradient():
         assert np.max(np.abs(G)) < 1e-12
 
 
+def test_cp_model_values_match_dense_reconstruction():
+    """The model evaluator behind the planted-value workload equals the dense
+    CP tensor (Sec. 2.2) read at the coordinates, order 3 and 4."""
+    rng = np.random.default_rng(24)
+    for dims in ((6, 5, 7), (4, 3, 5, 2)):
+        U = [rng.standard_normal((d, 3)) for d in dims]
+        cells = np.argwhere(rng.random(dims) < 0.6)
+        idx = [cells[:, k].astype(np.uint32) for k in range(len(dims))]
+        got = oracle.cp_model_values(dims, idx, U)
+        assert np.max(np.abs(got - brute.cp_dense(U)[tuple(cells.T)])) < 1e-12
+
+
 def test_gradient_is_minus_mttkrp_of_residual():
     rng = np.random.default_rng(23)
     dims = (5, 4, 6)

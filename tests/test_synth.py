@@ -50,10 +50,22 @@ def test_seeded_reproducible_and_seed_sensitive():
     assert int(a.idx[0].max()) < 8
 
 
-def test_planted_values_small_noise():
+def test_planted_values_are_model_plus_noise():
+    """The generator asks the caller for the planted model's values and adds
+    N(0, sigma^2) noise; a planted workload without an evaluator is refused."""
+    import pytest
     wl = synth.WORKLOADS["cploss3d"].scaled(nnz=3000, dims=(40, 40, 40))
-    X = synth.generate(wl)
+    with pytest.raises(ValueError):
+        synth.generate(wl)
+    seen = {}
+
+    def fixed(coords, planted):
+        seen["shapes"] = ([tuple(c.shape) for c in coords], [tuple(p.shape) for p in planted])
+        return torch.full((coords[0].numel(),), 3.0, dtype=torch.float64)
+
+    X = synth.generate(wl, model_values=fixed)
+    assert seen["shapes"] == ([(3000,)] * 3, [(40, 16)] * 3)
     assert X.planted is not None and X.planted[0].shape == (40, 16)
-    clean = synth.planted_values(X.idx, X.planted)
-    noise = (X.val - clean).double()
-    assert 0.005 < float(noise.std()) < 0.02
+    noise = (X.val - 3.0).double()
+    assert abs(float(noise.mean())) < 2e-3
+    assert 0.009 < float(noise.std()) < 0.011
