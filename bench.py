@@ -788,13 +788,12 @@ def e2e(pasta, synth, wl, dev, args, world):
     main = torch.cuda.current_stream(dev)
 
     def one():
-        idx = [t.to(dev, non_blocking=True) for t in idx_h]
-        val = val_h.to(dev, non_blocking=True)
+        # the COO arrays go from pinned host memory straight into the
+        # handle's creation-order copy; the factors follow on the side stream
+        X = pasta.CooTensor(wl.dims, idx_h, val_h, validate=False, device=dev)
         side.wait_stream(main)
         with torch.cuda.stream(side):
             Us = [u.to(dev, non_blocking=True) for u in Uh]
-        X = pasta.CooTensor(wl.dims, idx, val, validate=False)
-        del idx, val
         X.sort_by_mode(0)
         aux.wait_stream(main)
         sorted_ev = [None]
@@ -829,13 +828,10 @@ def e2e(pasta, synth, wl, dev, args, world):
         return t
 
     t = time.perf_counter()
-    idx = [t_.to(dev, non_blocking=True) for t_ in idx_h]
-    val = val_h.to(dev, non_blocking=True)
+    X = pasta.CooTensor(wl.dims, idx_h, val_h, validate=False, device=dev)
+    t = mark("create_with_coo_h2d", t)
     Us = [u.to(dev, non_blocking=True) for u in Uh]
-    t = mark("h2d", t)
-    X = pasta.CooTensor(wl.dims, idx, val, validate=False)
-    del idx, val
-    t = mark("create", t)
+    t = mark("factors_h2d", t)
     X.sort_all()
     t = mark("sort_all_modes", t)
     Ms = [pasta.mttkrp(X, Us, n) for n in range(N)]
@@ -846,21 +842,32 @@ def e2e(pasta, synth, wl, dev, args, world):
     X.close()
     del Ms, Us
     mark("destroy", t)
-    steps = max(2, min(args.steps, 10))
+    steps = max(2, min(args.steps, 20))
     torch.cuda.synchronize()
     # host-timed steps: Python's cyclic garbage collector is paused while
     # they run, as timeit does
     gc.collect()
     gc_was_on = gc.isenabled()
     gc.disable()
-    t0 = time.perf_counter()
+    # per step: host time, the main stream's device time (events), and the
+    # caching allocator's device allocations (to tell host stalls, device
+    # stalls and cudaMalloc calls apart)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    n_alloc = []
+    total = 0.0
     per_step = []
-    for _ in range(steps):
+    for k in range(steps):
+        a0 = torch.cuda.memory_stats(dev).get("num_device_alloc", 0)
         ts = time.perf_counter()
-        one()
-        per_step.append(round((time.perf_counter() - ts) * 1e3, 2))
+        ev[k][0].record()
+        one()  # ends with a device synchronisation
+        ev[k][1].record()
+        te = time.perf_counter() - ts
+        total += te
+        per_step.append(round(te * 1e3, 2))
+        n_alloc.append(torch.cuda.memory_stats(dev).get("num_device_alloc", 0) - a0)
     torch.cuda.synchronize()
-    dt = (time.perf_counter() - t0) / steps
+    dt = total / steps
     if gc_was_on:
         gc.enable()
     if world > 1:
@@ -872,10 +879,13 @@ def e2e(pasta, synth, wl, dev, args, world):
     return {"value": world * N * wl.nnz / dt, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": steps,
             "median_step_ms": sorted(per_step)[len(per_step) // 2],
-            "includes": ("H2D of COO+factors, create, sort every mode, MTTKRP every mode, D2H of outputs "
-                         "(factor upload and output downloads on a side stream; sorts of modes 1.. on a "
-                         "second stream, overlapping the MTTKRPs of the modes before)"),
-            "breakdown_ms": br, "per_step_ms": per_step}
+            "includes": ("create from pinned host COO (H2D straight into the handle's copy), H2D of factors, "
+                         "sort every mode, MTTKRP every mode, D2H of outputs (factor upload and output downloads "
+                         "on a side stream; sorts of modes N-1..1 on a second stream, overlapping the MTTKRPs "
+                         "of the modes sorted before)"),
+            "breakdown_ms": br, "per_step_ms": per_step,
+            "per_step_device_ms": [round(a.elapsed_time(b), 2) for a, b in ev],
+            "per_step_device_allocs": n_alloc}
 
 
 # ----------------------------------------------------------- CPU oracle --

@@ -101,12 +101,15 @@ int pasta_version(void);
  *   order  number of modes N
  *   dims   host array of N mode sizes
  *   nnz    number of stored entries (0 allowed)
- *   d_idx  host array of N device pointers; d_idx[k][m] is entry m's index in
- *          mode k (uint32, nnz elements each; any alignment)
- *   d_val  device pointer to nnz FP32 values
+ *   d_idx  host array of N pointers; d_idx[k][m] is entry m's index in mode k
+ *          (uint32, nnz elements each; any alignment)
+ *   d_val  pointer to nnz FP32 values
  *   flags  PASTA_CREATE_DEFAULT or PASTA_CREATE_NO_VALIDATE
- * The input arrays are only read, and may be freed once the stream has
- * passed this call.  Storage order is kept ("creation order").  Unless
+ * Each input array may be device memory or host memory: it is copied with
+ * cudaMemcpyAsync(..., cudaMemcpyDefault) on `stream`, so pinned host memory
+ * goes straight into the handle's copy (no device staging buffer).  The input
+ * arrays are only read, and may be freed once the stream has passed this
+ * call (pageable host memory: once the call returns).  Storage order is kept ("creation order").  Unless
  * PASTA_CREATE_NO_VALIDATE is given, a device scan counts out-of-range indices
  * and non-finite values and this call waits for it: PASTA_ERR_INDEX_OOB /
  * PASTA_ERR_NONFINITE are returned and no handle is made.  Duplicated
@@ -513,9 +516,11 @@ pasta_status pasta_hicoo_copy_out(pasta_coo X, uint32_t *d_bptr, uint32_t *const
  * pasta_hicoo_mttkrp -- the mode-n MTTKRP of pasta_mttkrp (Eq.
  * (mttkrp-init)), computed from the HiCOO copy (PASTA_ERR_NOT_SORTED if
  * absent) instead of a mode-sorted copy.  Same arguments and output.  The
- * copy is not ordered by the output mode, so rows are summed in two
- * register slots per lane group and added with vector atomics when evicted;
- * the summation order, and so the FP32 rounding, differs from pasta_mttkrp.
+ * copy is not ordered by the output mode, so rows are summed in two FP32
+ * register slots per lane group (at most one 512-entry tile each) and, when
+ * evicted, added with FP64 atomics into an FP64 image of M in the handle's
+ * scratch, which is then rounded into d_M; the summation order differs from
+ * pasta_mttkrp.  Calls on one handle that use the scratch must be ordered.
  * Covers FP32/BF16/FP16 factors, order 2..5, R * sizeof(element) = 16 L with
  * L a power of two, 16-byte aligned factors and output; otherwise
  * PASTA_ERR_UNSUPPORTED.

@@ -92,23 +92,32 @@ class CooTensor:
     ``idx``: one int32/uint32-valued tensor of nnz indices per mode (0-based,
     Sec. 5.1); ``val``: nnz FP32 values.  The data is copied into
     library-owned, padded SoA arrays; the inputs may be freed afterwards.
+    The inputs may be CUDA tensors or host tensors (then ``device`` names the
+    CUDA device, default the current one): pinned host tensors are copied
+    asynchronously on the current stream straight into the library's copy.
     """
 
     def __init__(self, dims: Sequence[int], idx: Sequence[torch.Tensor], val: torch.Tensor,
-                 validate: bool = True):
+                 validate: bool = True, device=None):
         dims = [int(d) for d in dims]
         order = len(dims)
         if len(idx) != order:
             raise ValueError("need one index tensor per mode")
-        if not val.is_cuda:
-            raise ValueError("val must be a CUDA tensor")
-        self.device = val.device
+        if val.is_cuda:
+            self.device = val.device
+        else:
+            # host tensors (pinned: copied asynchronously straight into the
+            # handle's copy; they are kept referenced until close())
+            self.device = torch.device(device) if device is not None else torch.device(
+                "cuda", torch.cuda.current_device())
+            if self.device.type != "cuda":
+                raise ValueError("device must be a CUDA device")
         self.dims = tuple(dims)
         self.order = order
         self.nnz = int(val.numel())
         idx_c = []
         for ix in idx:
-            if ix.device != self.device or ix.numel() != self.nnz:
+            if ix.device != val.device or ix.numel() != self.nnz:
                 raise ValueError("index tensors must be on val's device with nnz elements")
             if ix.dtype not in (torch.int32, torch.uint32):
                 raise TypeError("indices must be int32 (values < 2^31) or uint32")
@@ -127,6 +136,7 @@ class CooTensor:
         _lib.check(st, "pasta_coo_create")
         self._h = h
         self._sorted: set[int] = set()
+        self._host_refs = None if val.is_cuda else (idx_c, val_c)
 
     @property
     def handle(self) -> ctypes.c_void_p:
@@ -141,12 +151,14 @@ class CooTensor:
         t.device, t.dims, t.order, t.nnz = like.device, like.dims, like.order, like.nnz
         t._h = handle
         t._sorted = set()
+        t._host_refs = None
         return t
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None:
-            _lib.lib().pasta_coo_destroy(self._h)
+            _lib.lib().pasta_coo_destroy(self._h)  # synchronises the device
             self._h = None
+        self._host_refs = None
 
     def __del__(self):
         try:

@@ -237,7 +237,7 @@ pasta_status validate_coo(const pasta_coo_s *X, void *stream, uint64_t *bad_inde
 }
 
 // Handle construction shared by pasta_coo_create and the operations that
-// return a new tensor: copies the caller's (device) coordinates and, when
+// return a new tensor: copies the caller's (device or host) coordinates and, when
 // d_val is not NULL, values into a new creation-order copy (zero padding);
 // validates unless PASTA_CREATE_NO_VALIDATE.
 pasta_status make_handle(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,
@@ -292,12 +292,21 @@ pasta_status make_handle(pasta_coo *out, int order, const uint64_t *dims, uint64
         X->partials_cap = kPartialsCap;
     }
     if (st == PASTA_OK) {
+        // only the padding past nnz needs zeros; the copies below fill the rest
+        // (without values, the value array is zeroed whole)
         const size_t arr = (size_t)X->nnz_pad * 4;
-        e = cudaMemsetAsync(X->orig.block, 0, arr * (size_t)(order + 1), s);
+        const size_t tail = (size_t)(X->nnz_pad - nnz) * 4;
+        e = cudaSuccess;
+        for (int k = 0; k < order && e == cudaSuccess; ++k)
+            e = cudaMemsetAsync(X->orig.idx[k] + nnz, 0, tail, s);
+        if (e == cudaSuccess)
+            e = d_val ? cudaMemsetAsync(X->orig.val + nnz, 0, tail, s) : cudaMemsetAsync(X->orig.val, 0, arr, s);
+        // cudaMemcpyDefault: the source may be device memory or host memory
+        // (the copy direction follows the pointer under unified addressing)
         for (int k = 0; k < order && e == cudaSuccess && nnz > 0; ++k)
-            e = cudaMemcpyAsync(X->orig.idx[k], d_idx[k], nnz * 4, cudaMemcpyDeviceToDevice, s);
+            e = cudaMemcpyAsync(X->orig.idx[k], d_idx[k], nnz * 4, cudaMemcpyDefault, s);
         if (e == cudaSuccess && nnz > 0 && d_val)
-            e = cudaMemcpyAsync(X->orig.val, d_val, nnz * 4, cudaMemcpyDeviceToDevice, s);
+            e = cudaMemcpyAsync(X->orig.val, d_val, nnz * 4, cudaMemcpyDefault, s);
         if (e != cudaSuccess) st = cuda_fail(e, "copy-in");
     }
     if (st == PASTA_OK) X->orig.present = true;

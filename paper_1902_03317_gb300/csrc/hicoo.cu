@@ -390,7 +390,7 @@ struct HArgs {
     const T *U[N];
     const float *val;
     const uint32_t *tile_block;
-    float *M;
+    double *M;  // FP64 image of the output (converted to FP32 after the kernel)
     uint64_t nnz, ntiles;
     uint32_t R;
     int bits, L, lshift;
@@ -410,14 +410,20 @@ __device__ __forceinline__ uint4 ld_row16(const void *p, uint64_t pol) {
     return r;
 }
 
-template <int VEC> __device__ __forceinline__ void flush_row(float *M, uint32_t row, uint32_t R, int off,
+// A row slot's FP32 partial sums (at most one 512-entry tile's) are added
+// into the FP64 image of the output: an output row can receive a partial
+// from every tile (millions, for the short modes), and FP32 atomic sums of
+// that many terms drift beyond the FP32 MTTKRP's error bar.
+template <int VEC> __device__ __forceinline__ void flush_row(double *M, uint32_t row, uint32_t R, int off,
                                                              const float (&acc)[VEC]) {
-    float *d = M + (uint64_t)row * R + off;
+    double *d = M + (uint64_t)row * R + off;
 #pragma unroll
-    for (int e = 0; e < VEC; e += 4) {
-        const float v4[4] = {acc[e], acc[e + 1], acc[e + 2], acc[e + 3]};
-        RedAdd<float, 4>::run(d + e, v4);
-    }
+    for (int e = 0; e < VEC; ++e) atomicAdd(d + e, (double)acc[e]);
+}
+
+__global__ void k_to_f32(const double *src, float *dst, uint64_t n) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
 }
 
 template <typename T, int N, int MINB>
@@ -522,7 +528,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_hicoo_mttkrp(const HArgs<T, 
 }
 
 template <typename T, int N>
-pasta_status hrun(const pasta_coo_s *X, const void *const *U, int mode, int R, float *M, cudaStream_t s) {
+pasta_status hrun(const pasta_coo_s *X, const void *const *U, int mode, int R, double *M, cudaStream_t s) {
     const HicooCopy &H = X->hicoo;
     HArgs<T, N> a{};
     for (int p = 0; p < N; ++p) {
@@ -542,7 +548,7 @@ pasta_status hrun(const pasta_coo_s *X, const void *const *U, int mode, int R, f
     const Geometry g = make_geometry(R, 16 / (int)sizeof(T), (int)sizeof(T));
     a.L = g.L;
     a.lshift = g.lshift;
-    constexpr int MINB = N <= 3 ? 3 : 2;
+    constexpr int MINB = (N <= 3 && sizeof(T) == 4) ? 3 : 2;  // 16-bit rows widen to 8 FP64 adds per flush
     auto kern = k_hicoo_mttkrp<T, N, MINB>;
     int per_sm = 0;
     PASTA_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0));
@@ -556,7 +562,7 @@ pasta_status hrun(const pasta_coo_s *X, const void *const *U, int mode, int R, f
 }
 
 template <typename T>
-pasta_status hby_order(const pasta_coo_s *X, const void *const *U, int mode, int R, float *M, cudaStream_t s) {
+pasta_status hby_order(const pasta_coo_s *X, const void *const *U, int mode, int R, double *M, cudaStream_t s) {
     switch (X->order) {
         case 2: return hrun<T, 2>(X, U, mode, R, M, s);
         case 3: return hrun<T, 3>(X, U, mode, R, M, s);
@@ -568,22 +574,36 @@ pasta_status hby_order(const pasta_coo_s *X, const void *const *U, int mode, int
 
 }  // namespace
 
-pasta_status launch_hicoo_mttkrp(const pasta_coo_s *X, const void *const *U, pasta_dtype dt, int mode, int R,
+pasta_status launch_hicoo_mttkrp(pasta_coo_s *X, const void *const *U, pasta_dtype dt, int mode, int R,
                                  void *M, cudaStream_t s) {
     if (!stream_supported(dt, X->order, R, U, mode, M, 2)) {
         set_error("the HiCOO MTTKRP covers FP32/BF16/FP16 factors, order 2..5, R * sizeof(element) = 16 L "
                   "(L a power of two) and 16-byte aligned factors and output");
         return PASTA_ERR_UNSUPPORTED;
     }
-    PASTA_CUDA(cudaMemsetAsync(M, 0, (size_t)X->dims[mode] * (size_t)R * sizeof(float), s));
-    if (X->nnz == 0) return PASTA_OK;
-    float *Mf = static_cast<float *>(M);
-    switch (dt) {
-        case PASTA_F32: return hby_order<float>(X, U, mode, R, Mf, s);
-        case PASTA_BF16: return hby_order<__nv_bfloat16>(X, U, mode, R, Mf, s);
-        case PASTA_F16: return hby_order<__half>(X, U, mode, R, Mf, s);
-        default: return PASTA_ERR_UNSUPPORTED;
+    const uint64_t n = X->dims[mode] * (uint64_t)R;
+    if (X->nnz == 0) {
+        PASTA_CUDA(cudaMemsetAsync(M, 0, n * sizeof(float), s));
+        return PASTA_OK;
     }
+    // the FP64 image of M lives in the handle's scratch (calls on one handle
+    // are ordered, so it is not in use by a sort)
+    void *img = nullptr;
+    pasta_status st = handle_scratch(X, n * sizeof(double), &img);
+    if (st != PASTA_OK) return st;
+    double *M64 = static_cast<double *>(img);
+    PASTA_CUDA(cudaMemsetAsync(M64, 0, n * sizeof(double), s));
+    switch (dt) {
+        case PASTA_F32: st = hby_order<float>(X, U, mode, R, M64, s); break;
+        case PASTA_BF16: st = hby_order<__nv_bfloat16>(X, U, mode, R, M64, s); break;
+        case PASTA_F16: st = hby_order<__half>(X, U, mode, R, M64, s); break;
+        default: st = PASTA_ERR_UNSUPPORTED;
+    }
+    if (st != PASTA_OK) return st;
+    const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 8));
+    k_to_f32<<<blocks, 256, 0, s>>>(M64, static_cast<float *>(M), n);
+    PASTA_CUDA(cudaGetLastError());
+    return PASTA_OK;
 }
 
 }  // namespace pasta

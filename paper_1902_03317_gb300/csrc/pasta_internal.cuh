@@ -239,7 +239,7 @@ pasta_status launch_ttm(pasta_coo_s *X, int mode, const void *U, pasta_dtype dt,
 // HiCOO copy and its MTTKRP (hicoo.cu).
 pasta_status build_hicoo(pasta_coo_s *X, int bits, cudaStream_t stream);
 void free_hicoo(HicooCopy &H);
-pasta_status launch_hicoo_mttkrp(const pasta_coo_s *X, const void *const *U, pasta_dtype dt, int mode, int R,
+pasta_status launch_hicoo_mttkrp(pasta_coo_s *X, const void *const *U, pasta_dtype dt, int mode, int R,
                                  void *M, cudaStream_t stream);
 
 pasta_status launch_convert(const void *src, pasta_dtype st, void *dst, pasta_dtype dt,
