@@ -518,9 +518,11 @@ pasta_status pasta_hicoo_copy_out(pasta_coo X, uint32_t *d_bptr, uint32_t *const
  * absent) instead of a mode-sorted copy.  Same arguments and output.  The
  * copy is not ordered by the output mode, so rows are summed in two FP32
  * register slots per lane group (at most one 512-entry tile each) and, when
- * evicted, added with FP64 atomics into an FP64 image of M in the handle's
- * scratch, which is then rounded into d_M; the summation order differs from
- * pasta_mttkrp.  Calls on one handle that use the scratch must be ordered.
+ * evicted, added with FP64 atomics into FP64 images of M in the handle's
+ * scratch (block b into image b mod K, K images within 256 MB, at most 64),
+ * which are then summed and rounded into d_M; the summation order differs
+ * from pasta_mttkrp.  Calls on one handle that use the scratch must be
+ * ordered.
  * Covers FP32/BF16/FP16 factors, order 2..5, R * sizeof(element) = 16 L with
  * L a power of two, 16-byte aligned factors and output; otherwise
  * PASTA_ERR_UNSUPPORTED.

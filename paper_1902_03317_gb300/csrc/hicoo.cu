@@ -390,8 +390,10 @@ struct HArgs {
     const T *U[N];
     const float *val;
     const uint32_t *tile_block;
-    double *M;  // FP64 image of the output (converted to FP32 after the kernel)
+    double *M;  // FP64 images of the output: `copies` of dims[mode] x R (summed into FP32 after)
     uint64_t nnz, ntiles;
+    uint64_t copy_stride;  // elements per image
+    uint32_t copies;       // block b adds into image b % copies
     uint32_t R;
     int bits, L, lshift;
 };
@@ -411,9 +413,11 @@ __device__ __forceinline__ uint4 ld_row16(const void *p, uint64_t pol) {
 }
 
 // A row slot's FP32 partial sums (at most one 512-entry tile's) are added
-// into the FP64 image of the output: an output row can receive a partial
+// into an FP64 image of the output: an output row can receive a partial
 // from every tile (millions, for the short modes), and FP32 atomic sums of
-// that many terms drift beyond the FP32 MTTKRP's error bar.
+// that many terms drift beyond the FP32 MTTKRP's error bar.  Blocks spread
+// over several images (Sec. 5.3's privatization, per block instead of per
+// thread), so a hot row's additions queue on several addresses, not one.
 template <int VEC> __device__ __forceinline__ void flush_row(double *M, uint32_t row, uint32_t R, int off,
                                                              const float (&acc)[VEC]) {
     double *d = M + (uint64_t)row * R + off;
@@ -421,9 +425,13 @@ template <int VEC> __device__ __forceinline__ void flush_row(double *M, uint32_t
     for (int e = 0; e < VEC; ++e) atomicAdd(d + e, (double)acc[e]);
 }
 
-__global__ void k_to_f32(const double *src, float *dst, uint64_t n) {
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
-        dst[i] = (float)src[i];
+// dst[i] = FP32 of the sum over the images of element i.
+__global__ void k_images_to_f32(const double *src, uint32_t copies, uint64_t n, float *dst) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+        double acc = 0.0;
+        for (uint32_t c = 0; c < copies; ++c) acc += src[(uint64_t)c * n + i];
+        dst[i] = (float)acc;
+    }
 }
 
 template <typename T, int N, int MINB>
@@ -443,6 +451,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_hicoo_mttkrp(const HArgs<T, 
     for (int p = 1; p < N; ++p) ub[p] = reinterpret_cast<const char *>(a.U[p] + off);
     const uint64_t gid = ((uint64_t)blockIdx.x * (kThreads / 32) + warp) * G + grp;
     const uint64_t gstride = (uint64_t)gridDim.x * (kThreads / 32) * G;
+    double *const Mimg = a.M + (uint64_t)(blockIdx.x % a.copies) * a.copy_stride;
 
     for (uint64_t t = gid; t < a.ntiles; t += gstride) {
         uint64_t p = t * kHTile;
@@ -511,7 +520,7 @@ __global__ void __launch_bounds__(kThreads, MINB) k_hicoo_mttkrp(const HArgs<T, 
                     srow[1] = srow[0];
                     srow[0] = o;
                 } else {  // evict slot 1, shift slot 0 down
-                    if (srow[1] != kNoRow) flush_row<VEC>(a.M, srow[1], a.R, off, sacc[1]);
+                    if (srow[1] != kNoRow) flush_row<VEC>(Mimg, srow[1], a.R, off, sacc[1]);
 #pragma unroll
                     for (int e = 0; e < VEC; ++e) {
                         sacc[1][e] = sacc[0][e];
@@ -522,13 +531,14 @@ __global__ void __launch_bounds__(kThreads, MINB) k_hicoo_mttkrp(const HArgs<T, 
                 }
             }
         }
-        if (srow[0] != kNoRow) flush_row<VEC>(a.M, srow[0], a.R, off, sacc[0]);
-        if (srow[1] != kNoRow) flush_row<VEC>(a.M, srow[1], a.R, off, sacc[1]);
+        if (srow[0] != kNoRow) flush_row<VEC>(Mimg, srow[0], a.R, off, sacc[0]);
+        if (srow[1] != kNoRow) flush_row<VEC>(Mimg, srow[1], a.R, off, sacc[1]);
     }
 }
 
 template <typename T, int N>
-pasta_status hrun(const pasta_coo_s *X, const void *const *U, int mode, int R, double *M, cudaStream_t s) {
+pasta_status hrun(const pasta_coo_s *X, const void *const *U, int mode, int R, double *M, uint32_t copies,
+                  cudaStream_t s) {
     const HicooCopy &H = X->hicoo;
     HArgs<T, N> a{};
     for (int p = 0; p < N; ++p) {
@@ -541,6 +551,8 @@ pasta_status hrun(const pasta_coo_s *X, const void *const *U, int mode, int R, d
     a.val = H.val;
     a.tile_block = H.tile_block;
     a.M = M;
+    a.copies = copies;
+    a.copy_stride = X->dims[mode] * (uint64_t)R;
     a.nnz = X->nnz;
     a.ntiles = H.ntiles;
     a.R = (uint32_t)R;
@@ -562,12 +574,13 @@ pasta_status hrun(const pasta_coo_s *X, const void *const *U, int mode, int R, d
 }
 
 template <typename T>
-pasta_status hby_order(const pasta_coo_s *X, const void *const *U, int mode, int R, double *M, cudaStream_t s) {
+pasta_status hby_order(const pasta_coo_s *X, const void *const *U, int mode, int R, double *M, uint32_t copies,
+                       cudaStream_t s) {
     switch (X->order) {
-        case 2: return hrun<T, 2>(X, U, mode, R, M, s);
-        case 3: return hrun<T, 3>(X, U, mode, R, M, s);
-        case 4: return hrun<T, 4>(X, U, mode, R, M, s);
-        case 5: return hrun<T, 5>(X, U, mode, R, M, s);
+        case 2: return hrun<T, 2>(X, U, mode, R, M, copies, s);
+        case 3: return hrun<T, 3>(X, U, mode, R, M, copies, s);
+        case 4: return hrun<T, 4>(X, U, mode, R, M, copies, s);
+        case 5: return hrun<T, 5>(X, U, mode, R, M, copies, s);
     }
     return PASTA_ERR_UNSUPPORTED;
 }
@@ -586,22 +599,25 @@ pasta_status launch_hicoo_mttkrp(pasta_coo_s *X, const void *const *U, pasta_dty
         PASTA_CUDA(cudaMemsetAsync(M, 0, n * sizeof(float), s));
         return PASTA_OK;
     }
-    // the FP64 image of M lives in the handle's scratch (calls on one handle
-    // are ordered, so it is not in use by a sort)
+    // The FP64 images of M live in the handle's scratch (calls on one handle
+    // are ordered, so it is not in use by a sort): as many as fit 256 MB, at
+    // most 64, at least one.
+    const uint64_t img_bytes = n * sizeof(double);
+    const uint32_t copies = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(64, (256ull << 20) / img_bytes));
     void *img = nullptr;
-    pasta_status st = handle_scratch(X, n * sizeof(double), &img);
+    pasta_status st = handle_scratch(X, img_bytes * copies, &img);
     if (st != PASTA_OK) return st;
     double *M64 = static_cast<double *>(img);
-    PASTA_CUDA(cudaMemsetAsync(M64, 0, n * sizeof(double), s));
+    PASTA_CUDA(cudaMemsetAsync(M64, 0, img_bytes * copies, s));
     switch (dt) {
-        case PASTA_F32: st = hby_order<float>(X, U, mode, R, M64, s); break;
-        case PASTA_BF16: st = hby_order<__nv_bfloat16>(X, U, mode, R, M64, s); break;
-        case PASTA_F16: st = hby_order<__half>(X, U, mode, R, M64, s); break;
+        case PASTA_F32: st = hby_order<float>(X, U, mode, R, M64, copies, s); break;
+        case PASTA_BF16: st = hby_order<__nv_bfloat16>(X, U, mode, R, M64, copies, s); break;
+        case PASTA_F16: st = hby_order<__half>(X, U, mode, R, M64, copies, s); break;
         default: st = PASTA_ERR_UNSUPPORTED;
     }
     if (st != PASTA_OK) return st;
     const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 8));
-    k_to_f32<<<blocks, 256, 0, s>>>(M64, static_cast<float *>(M), n);
+    k_images_to_f32<<<blocks, 256, 0, s>>>(M64, copies, n, static_cast<float *>(M));
     PASTA_CUDA(cudaGetLastError());
     return PASTA_OK;
 }
