@@ -787,14 +787,20 @@ def e2e(pasta, synth, wl, dev, args, world):
     aux = torch.cuda.Stream(device=dev)
     main = torch.cuda.current_stream(dev)
 
-    def one():
+    def one(marks=None):
         # the COO arrays go from pinned host memory straight into the
         # handle's creation-order copy; the factors follow on the side stream
+        # (marks: events recorded on the main stream after the create with
+        # its copy and after the first sort, for the per-step phase times)
         X = pasta.CooTensor(wl.dims, idx_h, val_h, validate=False, device=dev)
+        if marks is not None:
+            marks[0].record()
         side.wait_stream(main)
         with torch.cuda.stream(side):
             Us = [u.to(dev, non_blocking=True) for u in Uh]
         X.sort_by_mode(0)
+        if marks is not None:
+            marks[1].record()
         aux.wait_stream(main)
         sorted_ev = [None]
         with torch.cuda.stream(aux):
@@ -853,6 +859,7 @@ def e2e(pasta, synth, wl, dev, args, world):
     # caching allocator's device allocations (to tell host stalls, device
     # stalls and cudaMalloc calls apart)
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    mk = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
     n_alloc = []
     total = 0.0
     per_step = []
@@ -860,7 +867,7 @@ def e2e(pasta, synth, wl, dev, args, world):
         a0 = torch.cuda.memory_stats(dev).get("num_device_alloc", 0)
         ts = time.perf_counter()
         ev[k][0].record()
-        one()  # ends with a device synchronisation
+        one(mk[k])  # ends with a device synchronisation
         ev[k][1].record()
         te = time.perf_counter() - ts
         total += te
@@ -885,6 +892,9 @@ def e2e(pasta, synth, wl, dev, args, world):
                          "of the modes sorted before)"),
             "breakdown_ms": br, "per_step_ms": per_step,
             "per_step_device_ms": [round(a.elapsed_time(b), 2) for a, b in ev],
+            "per_step_phases_ms": [[round(e0.elapsed_time(m0), 2), round(m0.elapsed_time(m1), 2),
+                                    round(m1.elapsed_time(e1), 2)] for (e0, e1), (m0, m1) in zip(ev, mk)],
+            "phases": "create with the COO H2D; first sort; the rest (factor upload, later sorts, MTTKRPs, downloads)",
             "per_step_device_allocs": n_alloc}
 
 

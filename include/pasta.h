@@ -249,9 +249,8 @@ pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype 
  * deployment variant of the same forward kernel.
  *
  * Who needs it: code that may not call cudaMalloc (or any allocating library
- * routine) where it computes the loss -- work recorded into a stream capture
- * owned by another framework, real-time or callback contexts, processes whose
- * device memory belongs to a different allocator.  pasta_coo_create copies
+ * routine) where it computes the loss -- real-time or callback contexts,
+ * processes whose device memory belongs to a different allocator.  pasta_coo_create copies
  * the tensor and keeps per-handle scratch, so it is not usable there; this
  * call reads the caller's own arrays and keeps its scratch (the FP64 partial
  * sums of the loss, one per thread block) in a fixed device array inside the
@@ -275,12 +274,11 @@ pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype 
  * that many blocks), and nothing in it has to start at zero.  All calls share
  * it: calls whose work overlaps on the GPU (for example on two streams at
  * once) race and give wrong losses; calls in sequence on one stream are safe.
- * The first call on a device looks up the array's device address for that
- * device (cudaGetSymbolAddress, which may load the library's device code), so
- * make the first call on each device before any stream capture.  The address
- * is kept for the life of the process: after cudaDeviceReset on a device the
- * library's device code is reloaded and the array may move, so this entry
- * point must not be used on that device again in the same process.
+ * Every call looks up the array's device address on the current device
+ * (cudaGetSymbolAddress).  The first call on a device may load the library's
+ * device code, which allocates, and so may the first call after
+ * cudaDeviceReset (the array may then sit at a new address, which the lookup
+ * finds); later calls allocate nothing.
  */
 #define PASTA_NOALLOC_MAX_PARTIALS 4096
 

@@ -16,7 +16,6 @@
 // Calls share it, so calls whose work overlaps on the GPU race; successive
 // calls on one stream are fine.  Nothing in it needs clearing: every block of
 // a launch writes its own partial and the final sum reads only those.
-#include <mutex>
 
 #include "pasta_internal.cuh"
 
@@ -28,26 +27,22 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_partials[kNoallocPartials];
 
-// Device address of g_noalloc_partials per device, resolved once per device
-// with that device current (in host code the symbol's name is only a
-// host-side stand-in and must not be passed to a kernel).
-std::mutex g_mu;
-double *g_addr[kMaxDevices] = {};
-
+// Device address of g_noalloc_partials on the current device, looked up on
+// every call (in host code the symbol's name is only a host-side stand-in and
+// must not be passed to a kernel).  Not cached: after cudaDeviceReset the
+// module is loaded again and the array may sit elsewhere.  The lookup itself
+// allocates nothing once the module is loaded (the first call on a device,
+// and the first after a reset, may load it).
 pasta_status partials_address(int device, double **out) {
     if (device < 0 || device >= kMaxDevices) {
         set_error("device ordinal %d beyond the %d devices this entry point supports", device,
                   kMaxDevices);
         return PASTA_ERR_UNSUPPORTED;
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_partials)");
-        g_addr[device] = static_cast<double *>(p);
-    }
-    *out = g_addr[device];
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_partials)");
+    *out = static_cast<double *>(p);
     return PASTA_OK;
 }
 
