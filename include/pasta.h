@@ -107,9 +107,10 @@ int pasta_version(void);
  *   flags  PASTA_CREATE_DEFAULT or PASTA_CREATE_NO_VALIDATE
  * Each input array may be device memory or host memory: it is copied with
  * cudaMemcpyAsync(..., cudaMemcpyDefault) on `stream`, so pinned host memory
- * goes straight into the handle's copy (no device staging buffer).  The input
- * arrays are only read, and may be freed once the stream has passed this
- * call (pageable host memory: once the call returns).  Storage order is kept ("creation order").  Unless
+ * goes straight into the handle's copy (no device staging buffer; read by a
+ * kernel as pasta_memcpy does).  The input arrays are only read, and may be
+ * freed once the stream has passed this call (pageable host memory: once the
+ * call returns).  Storage order is kept ("creation order").  Unless
  * PASTA_CREATE_NO_VALIDATE is given, a device scan counts out-of-range indices
  * and non-finite values and this call waits for it: PASTA_ERR_INDEX_OOB /
  * PASTA_ERR_NONFINITE are returned and no handle is made.  Duplicated
@@ -527,6 +528,22 @@ pasta_status pasta_hicoo_copy_out(pasta_coo X, uint32_t *d_bptr, uint32_t *const
  */
 pasta_status pasta_hicoo_mttkrp(pasta_coo X, const void *const *d_U, pasta_dtype u_dtype, int mode, int R,
                                 void *d_M, void *stream);
+
+/*
+ * pasta_memcpy -- copy `bytes` from src to dst on `stream` (asynchronous).
+ * Either pointer may be device memory, pinned host memory or pageable host
+ * memory.  Where one side is pinned host memory, both are 16-byte aligned and
+ * bytes is a multiple of 4, a kernel moves the data (the SMs read or write
+ * the host memory over the host link) instead of the copy engine; otherwise
+ * cudaMemcpyAsync does (pageable memory: it returns once the source is read).
+ * Host memory must stay allocated, and unchanged or unread, until the stream
+ * has passed the copy.  pasta_coo_create copies its inputs the same way.
+ * Not a paper operation: measured on GB300, copy-engine transfers between
+ * pinned host memory and the GPU stalled for 20-90 ms about every 0.4 s in
+ * some runs while SM-driven ones did not, at the same ~210 GB/s.
+ * PASTA_ERR_INVALID_ARG for a NULL pointer with bytes > 0.
+ */
+pasta_status pasta_memcpy(void *dst, const void *src, uint64_t bytes, void *stream);
 
 /*
  * pasta_set_grid_cap -- upper bound on the thread blocks of every MTTKRP and

@@ -6,7 +6,7 @@ The compute path is libpasta, a C-ABI CUDA library for sm_103a
 and a thin torch-facing API.  Nothing here computes on the CPU: if the
 library is missing, calls fail with a RuntimeError.
 """
-from .api import (CooTensor, CPLoss, acc_dtype, convert, cp_als, cp_als_sweep, cp_loss,  # noqa: F401
+from .api import (CooTensor, CPLoss, acc_dtype, convert, copy_, cp_als, cp_als_sweep, cp_loss,  # noqa: F401
                   cp_loss_bwd, cp_loss_fwd, cp_loss_fwd_bwd, fiber_coords, fibers, gather_probe, grid_cap, hicoo,
                   hicoo_copy_out, hicoo_mttkrp, mttkrp, mttkrp_range, cp_loss_fwd_bwd_range,
                   tew_eq, ts, ttm, ttv, use_torch_allocator)
@@ -15,4 +15,4 @@ from ._lib import PastaError  # noqa: F401
 __all__ = ["CooTensor", "CPLoss", "cp_loss", "cp_loss_fwd", "cp_loss_bwd", "cp_loss_fwd_bwd", "mttkrp",
            "cp_als_sweep", "cp_als", "tew_eq", "ts", "fibers", "fiber_coords", "ttm", "ttv", "convert",
            "acc_dtype", "use_torch_allocator", "grid_cap", "gather_probe", "hicoo", "hicoo_copy_out",
-           "hicoo_mttkrp", "mttkrp_range", "cp_loss_fwd_bwd_range", "PastaError"]
+           "hicoo_mttkrp", "mttkrp_range", "cp_loss_fwd_bwd_range", "copy_", "PastaError"]

@@ -65,6 +65,7 @@ SIGNATURES = {
     "pasta_hicoo_copy_out": (_I, [_P, _P, _P, _P, _P, _P]),
     "pasta_hicoo_mttkrp": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "pasta_get_grid_cap": (_I, []),
+    "pasta_memcpy": (_I, [_P, _P, _U64, _P]),
 }
 
 _lock = threading.Lock()

@@ -623,3 +623,24 @@ class grid_cap:
     def __exit__(self, *exc):
         _lib.check(_lib.lib().pasta_set_grid_cap(self._prev), "pasta_set_grid_cap")
         return False
+
+
+def copy_(dst: torch.Tensor, src: torch.Tensor) -> torch.Tensor:
+    """``dst`` <- ``src`` through ``pasta_memcpy`` on the current stream of
+    the CUDA tensor's device: same number of bytes, both contiguous; either
+    may be a CUDA tensor or a host tensor.  Between pinned host memory and the
+    GPU the SMs move the data instead of the copy engine.  Asynchronous like
+    ``Tensor.copy_(..., non_blocking=True)``: keep host tensors alive and
+    untouched until the stream has passed the copy.  Returns ``dst``."""
+    if not (dst.is_contiguous() and src.is_contiguous()):
+        raise ValueError("copy_ needs contiguous tensors")
+    nbytes = dst.numel() * dst.element_size()
+    if nbytes != src.numel() * src.element_size():
+        raise ValueError("copy_ needs tensors of the same size in bytes")
+    dev = dst.device if dst.is_cuda else src.device
+    if dev.type != "cuda":
+        raise ValueError("copy_ needs one CUDA tensor")
+    with torch.cuda.device(dev):
+        st = _lib.lib().pasta_memcpy(dst.data_ptr(), src.data_ptr(), nbytes, _stream(dev))
+    _lib.check(st, "pasta_memcpy")
+    return dst

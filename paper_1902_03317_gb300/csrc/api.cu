@@ -236,6 +236,66 @@ pasta_status validate_coo(const pasta_coo_s *X, void *stream, uint64_t *bad_inde
     return PASTA_OK;
 }
 
+// n 32-bit words from src to dst, 16 bytes per access where possible; either
+// side may be pinned host memory (the SMs then move the data over the host
+// link).  Each thread keeps four 16-byte loads in flight, so a small grid
+// covers the link's latency and leaves most SMs to kernels running beside it.
+constexpr int kCopyThreads = 512;
+constexpr int kCopyIlp = 4;
+__global__ void __launch_bounds__(kCopyThreads) k_copy_words(const uint32_t *src, uint32_t *dst, uint64_t n) {
+    const uint64_t n4 = n / 4;
+    const uint64_t stride = (uint64_t)gridDim.x * kCopyThreads;
+    const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+    uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+    for (uint64_t i = (uint64_t)blockIdx.x * kCopyThreads + threadIdx.x; i < n4; i += stride * kCopyIlp) {
+        uint4 v[kCopyIlp];
+#pragma unroll
+        for (int k = 0; k < kCopyIlp; ++k)
+            if (i + k * stride < n4) v[k] = s4[i + k * stride];
+#pragma unroll
+        for (int k = 0; k < kCopyIlp; ++k)
+            if (i + k * stride < n4) d4[i + k * stride] = v[k];
+    }
+    for (uint64_t i = 4 * n4 + (uint64_t)blockIdx.x * kCopyThreads + threadIdx.x; i < n; i += stride) dst[i] = src[i];
+}
+
+// Device-side address of p if it is pinned host memory the device can reach,
+// else NULL (device memory, pageable memory, or an unknown pointer).
+const void *pinned_device_address(const void *p) {
+    cudaPointerAttributes pa{};
+    if (cudaPointerGetAttributes(&pa, p) != cudaSuccess) {
+        cudaGetLastError();  // clear the failed query
+        return nullptr;
+    }
+    return pa.type == cudaMemoryTypeHost ? pa.devicePointer : nullptr;
+}
+
+// Copy of `bytes` on stream s.  Where one side is pinned host memory, both
+// sides are 16-byte aligned and the size is whole words, a kernel moves the
+// data (SM loads and stores over the host link) instead of the copy engine:
+// measured on GB300, copy-engine transfers stalled for 20-90 ms about every
+// 0.4 s in some runs while SM-driven ones at the same ~210 GB/s did not.
+// Anything else goes through cudaMemcpyAsync (direction from the pointers).
+cudaError_t copy_bytes(void *dst, const void *src, uint64_t bytes, int num_sms, cudaStream_t s) {
+    if (bytes == 0) return cudaSuccess;
+    const bool aligned = ((reinterpret_cast<uintptr_t>(dst) | reinterpret_cast<uintptr_t>(src)) & 15) == 0;
+    if (aligned && bytes % 4 == 0) {
+        const void *hs = pinned_device_address(src);
+        void *hd = const_cast<void *>(pinned_device_address(dst));
+        if (hs || hd) {
+            // one block per 8 SMs: 4 x 16 bytes in flight per thread is enough
+            // for the host link's ~210 GB/s
+            const uint64_t n = bytes / 4;
+            const uint64_t want = (n / 4 + (uint64_t)kCopyThreads * kCopyIlp - 1) / ((uint64_t)kCopyThreads * kCopyIlp);
+            const int blocks = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)std::max(1, num_sms / 8)));
+            k_copy_words<<<blocks, kCopyThreads, 0, s>>>(static_cast<const uint32_t *>(hs ? hs : src),
+                                                        static_cast<uint32_t *>(hd ? hd : dst), n);
+            return cudaGetLastError();
+        }
+    }
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
+}
+
 // Handle construction shared by pasta_coo_create and the operations that
 // return a new tensor: copies the caller's (device or host) coordinates and, when
 // d_val is not NULL, values into a new creation-order copy (zero padding);
@@ -301,12 +361,11 @@ pasta_status make_handle(pasta_coo *out, int order, const uint64_t *dims, uint64
             e = cudaMemsetAsync(X->orig.idx[k] + nnz, 0, tail, s);
         if (e == cudaSuccess)
             e = d_val ? cudaMemsetAsync(X->orig.val + nnz, 0, tail, s) : cudaMemsetAsync(X->orig.val, 0, arr, s);
-        // cudaMemcpyDefault: the source may be device memory or host memory
-        // (the copy direction follows the pointer under unified addressing)
+        // the source may be device memory or host memory (copy_bytes)
         for (int k = 0; k < order && e == cudaSuccess && nnz > 0; ++k)
-            e = cudaMemcpyAsync(X->orig.idx[k], d_idx[k], nnz * 4, cudaMemcpyDefault, s);
+            e = copy_bytes(X->orig.idx[k], d_idx[k], nnz * 4, X->num_sms, s);
         if (e == cudaSuccess && nnz > 0 && d_val)
-            e = cudaMemcpyAsync(X->orig.val, d_val, nnz * 4, cudaMemcpyDefault, s);
+            e = copy_bytes(X->orig.val, d_val, nnz * 4, X->num_sms, s);
         if (e != cudaSuccess) st = cuda_fail(e, "copy-in");
     }
     if (st == PASTA_OK) X->orig.present = true;
@@ -956,6 +1015,20 @@ pasta_status pasta_hicoo_mttkrp(pasta_coo X, const void *const *d_U, pasta_dtype
         return PASTA_ERR_NOT_SORTED;
     }
     return launch_hicoo_mttkrp(X, d_U, u_dtype, mode, R, d_M, static_cast<cudaStream_t>(stream));
+}
+
+pasta_status pasta_memcpy(void *dst, const void *src, uint64_t bytes, void *stream) {
+    if (bytes == 0) return PASTA_OK;
+    if (!dst || !src) {
+        set_error("dst or src is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = copy_bytes(dst, src, bytes, sms, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return cuda_fail(e, "pasta_memcpy");
+    return PASTA_OK;
 }
 
 pasta_status pasta_set_grid_cap(int max_blocks) {

@@ -161,3 +161,33 @@ def test_create_from_host_memory(pinned):
         assert all(torch.equal(x, y) for x, y in zip(sa, sb))
     Xa.close()
     Xb.close()
+
+
+@pytest.mark.parametrize("nbytes", [4, 12, 16, 4100, 1 << 20, (1 << 20) + 12])
+def test_memcpy_every_direction(nbytes):
+    """pasta_memcpy (copy_): pinned host -> device, device -> pinned host,
+    device -> device and pageable host -> device, bit for bit, at sizes with
+    and without a ragged tail of words."""
+    n = nbytes // 4
+    g = torch.Generator().manual_seed(nbytes)
+    h = torch.randint(-2**31, 2**31 - 1, (n,), generator=g, dtype=torch.int32)
+    hp = h.pin_memory()
+    d = torch.empty(n, dtype=torch.int32, device=G.DEV)
+    G.pasta.copy_(d, hp)
+    torch.cuda.synchronize()
+    assert torch.equal(d.cpu(), h)
+    back = torch.zeros(n, dtype=torch.int32).pin_memory()
+    G.pasta.copy_(back, d)
+    torch.cuda.synchronize()
+    assert torch.equal(back, h)
+    d2 = torch.empty_like(d)
+    G.pasta.copy_(d2, d)
+    d3 = torch.empty_like(d)
+    G.pasta.copy_(d3, h)  # pageable source
+    torch.cuda.synchronize()
+    assert torch.equal(d2.cpu(), h) and torch.equal(d3.cpu(), h)
+    # an offset view (4-byte aligned, not 16): the copy-engine path
+    if n > 2:
+        G.pasta.copy_(d[1:], hp[1:])
+        torch.cuda.synchronize()
+        assert torch.equal(d.cpu(), h)
