@@ -792,13 +792,14 @@ def e2e(pasta, synth, wl, dev, args, world):
         # handle's creation-order copy; the factors follow on the side stream
         # (marks: events recorded on the main stream after the create with
         # its copy and after the first sort, for the per-step phase times)
-        X = pasta.CooTensor(wl.dims, idx_h, val_h, validate=False, device=dev)
+        # (create and the mode-0 sort in one call: the second half of the COO
+        # is copied in while the first half sorts)
+        X = pasta.CooTensor(wl.dims, idx_h, val_h, validate=False, device=dev, sort_mode=0)
         if marks is not None:
             marks[0].record()
         side.wait_stream(main)
         with torch.cuda.stream(side):
             Us = [pasta.copy_(torch.empty(u.shape, dtype=u.dtype, device=dev), u) for u in Uh]
-        X.sort_by_mode(0)
         if marks is not None:
             marks[1].record()
         aux.wait_stream(main)
@@ -886,16 +887,18 @@ def e2e(pasta, synth, wl, dev, args, world):
     return {"value": world * N * wl.nnz / dt, "unit": "nnz/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": dt * 1e3, "steps": steps,
             "median_step_ms": sorted(per_step)[len(per_step) // 2],
-            "includes": ("create from pinned host COO (H2D straight into the handle's copy), H2D of factors, "
-                         "sort every mode, MTTKRP every mode, D2H of outputs (factor upload and output downloads "
-                         "on a side stream; sorts of modes N-1..1 on a second stream, overlapping the MTTKRPs "
-                         "of the modes sorted before); every host<->device copy through the library "
-                         "(pasta_coo_create, pasta_memcpy: SM-driven copies of pinned host memory)"),
+            "includes": ("create from pinned host COO with the mode-0 sort (pasta_coo_create_sorted: the second "
+                         "half copied in while the first half sorts, then a merge), H2D of factors, sorts of the "
+                         "other modes, MTTKRP every mode, D2H of outputs (factor upload and output downloads on a "
+                         "side stream; sorts of modes N-1..1 on a second stream, overlapping the MTTKRPs of the "
+                         "modes sorted before); every host<->device copy through the library (SM-driven copies "
+                         "of pinned host memory)"),
             "breakdown_ms": br, "per_step_ms": per_step,
             "per_step_device_ms": [round(a.elapsed_time(b), 2) for a, b in ev],
             "per_step_phases_ms": [[round(e0.elapsed_time(m0), 2), round(m0.elapsed_time(m1), 2),
                                     round(m1.elapsed_time(e1), 2)] for (e0, e1), (m0, m1) in zip(ev, mk)],
-            "phases": "create with the COO H2D; first sort; the rest (factor upload, later sorts, MTTKRPs, downloads)",
+            "phases": ("create with the COO H2D and the mode-0 sort (overlapped); the factor upload's issue; "
+                       "the rest (later sorts, MTTKRPs, downloads)"),
             "per_step_device_allocs": n_alloc}
 
 

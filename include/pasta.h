@@ -120,6 +120,22 @@ pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, u
                               const uint32_t *const *d_idx, const float *d_val,
                               unsigned flags, void *stream);
 
+/*
+ * pasta_coo_create_sorted -- pasta_coo_create followed by
+ * pasta_coo_sort_by_mode(mode), with the same arguments, result and errors,
+ * but overlapped: for at least 2^22 entries in pinned host memory (every
+ * array 16-byte aligned) whose sort key holds every index, the first half of
+ * the entries is copied in and sorted while the second half is copied (on a
+ * high-priority stream of the library's own, joined back to `stream`), then
+ * the second half is sorted and the two sorted halves are merged (stable,
+ * ties to the first half: the order one sort gives).  Otherwise it runs the
+ * two calls.  The sort's scratch grows to about 24 bytes per entry.
+ * PASTA_ERR_INVALID_ARG also for mode outside [0, order).
+ */
+pasta_status pasta_coo_create_sorted(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,
+                                     const uint32_t *const *d_idx, const float *d_val, unsigned flags,
+                                     int mode, void *stream);
+
 /* Free the handle and every copy it owns (synchronises the device). NULL is a no-op. */
 pasta_status pasta_coo_destroy(pasta_coo X);
 

@@ -66,6 +66,7 @@ SIGNATURES = {
     "pasta_hicoo_mttkrp": (_I, [_P, _P, _I, _I, _I, _P, _P]),
     "pasta_get_grid_cap": (_I, []),
     "pasta_memcpy": (_I, [_P, _P, _U64, _P]),
+    "pasta_coo_create_sorted": (_I, [_P, _I, _P, _U64, _P, _P, ctypes.c_uint, _I, _P]),
 }
 
 _lock = threading.Lock()

@@ -95,10 +95,12 @@ class CooTensor:
     The inputs may be CUDA tensors or host tensors (then ``device`` names the
     CUDA device, default the current one): pinned host tensors are copied
     asynchronously on the current stream straight into the library's copy.
+    ``sort_mode``: also build that mode's sorted copy in the same call
+    (``pasta_coo_create_sorted``, which overlaps the copy-in with the sort).
     """
 
     def __init__(self, dims: Sequence[int], idx: Sequence[torch.Tensor], val: torch.Tensor,
-                 validate: bool = True, device=None):
+                 validate: bool = True, device=None, sort_mode: int | None = None):
         dims = [int(d) for d in dims]
         order = len(dims)
         if len(idx) != order:
@@ -127,15 +129,23 @@ class CooTensor:
             raise TypeError("values must be float32")
         _ensure_allocator()
         h = ctypes.c_void_p()
+        flags = _lib.PASTA_CREATE_DEFAULT if validate else _lib.PASTA_CREATE_NO_VALIDATE
         with torch.cuda.device(self.device):
-            st = _lib.lib().pasta_coo_create(
-                ctypes.byref(h), order, _lib.u64_array(dims), self.nnz,
-                _lib.ptr_array([t.data_ptr() for t in idx_c]), val_c.data_ptr(),
-                _lib.PASTA_CREATE_DEFAULT if validate else _lib.PASTA_CREATE_NO_VALIDATE,
-                _stream(self.device))
-        _lib.check(st, "pasta_coo_create")
+            if sort_mode is None:
+                st = _lib.lib().pasta_coo_create(
+                    ctypes.byref(h), order, _lib.u64_array(dims), self.nnz,
+                    _lib.ptr_array([t.data_ptr() for t in idx_c]), val_c.data_ptr(), flags,
+                    _stream(self.device))
+            else:
+                # create and sort `sort_mode` in one call (pasta_coo_create_sorted:
+                # copy-in and sort overlapped for large pinned host inputs)
+                st = _lib.lib().pasta_coo_create_sorted(
+                    ctypes.byref(h), order, _lib.u64_array(dims), self.nnz,
+                    _lib.ptr_array([t.data_ptr() for t in idx_c]), val_c.data_ptr(), flags,
+                    int(sort_mode), _stream(self.device))
+        _lib.check(st, "pasta_coo_create" if sort_mode is None else "pasta_coo_create_sorted")
         self._h = h
-        self._sorted: set[int] = set()
+        self._sorted: set[int] = set() if sort_mode is None else {int(sort_mode)}
         self._host_refs = None if val.is_cuda else (idx_c, val_c)
 
     @property

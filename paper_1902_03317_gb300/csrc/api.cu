@@ -10,6 +10,7 @@
 #include <mutex>
 #include <new>
 
+#include "host_copy.cuh"
 #include "pasta_internal.cuh"
 #include "stream_kernels.cuh"
 
@@ -296,6 +297,10 @@ cudaError_t copy_bytes(void *dst, const void *src, uint64_t bytes, int num_sms, 
     return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s);
 }
 
+// make_handle flag (never accepted from callers): allocate and pad the
+// creation-order copy but leave the copy-in and the validation to the caller.
+constexpr unsigned kCreateDeferCopy = 1u << 30;
+
 // Handle construction shared by pasta_coo_create and the operations that
 // return a new tensor: copies the caller's (device or host) coordinates and, when
 // d_val is not NULL, values into a new creation-order copy (zero padding);
@@ -361,15 +366,17 @@ pasta_status make_handle(pasta_coo *out, int order, const uint64_t *dims, uint64
             e = cudaMemsetAsync(X->orig.idx[k] + nnz, 0, tail, s);
         if (e == cudaSuccess)
             e = d_val ? cudaMemsetAsync(X->orig.val + nnz, 0, tail, s) : cudaMemsetAsync(X->orig.val, 0, arr, s);
-        // the source may be device memory or host memory (copy_bytes)
-        for (int k = 0; k < order && e == cudaSuccess && nnz > 0; ++k)
+        // the source may be device memory or host memory (copy_bytes); with
+        // kCreateDeferCopy the caller copies (and validates) itself
+        const bool copy = !(flags & kCreateDeferCopy);
+        for (int k = 0; k < order && e == cudaSuccess && nnz > 0 && copy; ++k)
             e = copy_bytes(X->orig.idx[k], d_idx[k], nnz * 4, X->num_sms, s);
-        if (e == cudaSuccess && nnz > 0 && d_val)
+        if (e == cudaSuccess && nnz > 0 && d_val && copy)
             e = copy_bytes(X->orig.val, d_val, nnz * 4, X->num_sms, s);
         if (e != cudaSuccess) st = cuda_fail(e, "copy-in");
     }
     if (st == PASTA_OK) X->orig.present = true;
-    if (st == PASTA_OK && !(flags & PASTA_CREATE_NO_VALIDATE)) {
+    if (st == PASTA_OK && !(flags & (PASTA_CREATE_NO_VALIDATE | kCreateDeferCopy))) {
         uint64_t bi = 0, bv = 0;
         st = validate_coo(X, stream, &bi, &bv);
         if (st == PASTA_OK && bi) {
@@ -426,6 +433,77 @@ pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, u
         return PASTA_ERR_INVALID_ARG;
     }
     return pasta::make_handle(out, order, dims, nnz, d_idx, d_val, flags, stream);
+}
+
+pasta_status pasta_coo_create_sorted(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,
+                                     const uint32_t *const *d_idx, const float *d_val, unsigned flags, int mode,
+                                     void *stream) {
+    if (flags & ~PASTA_CREATE_NO_VALIDATE) {
+        set_error("unknown flags 0x%x", flags);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (!out) {
+        set_error("out is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (order < 2 || order > PASTA_MAX_ORDER || !dims || mode < 0 || mode >= order) {
+        set_error("order must be in [2, %d], dims non-NULL and mode in [0, order)", PASTA_MAX_ORDER);
+        return PASTA_ERR_INVALID_ARG;
+    }
+    if (nnz > 0 && (!d_val || !d_idx)) {
+        set_error("d_idx or d_val is NULL");
+        return PASTA_ERR_INVALID_ARG;
+    }
+    // the overlapped path: large tensors in pinned host memory (16-byte
+    // aligned) whose sort key holds every index
+    int key_bits = 0;
+    for (int k = 0; k < order; ++k) {
+        uint64_t d = dims[k] ? dims[k] - 1 : 0;
+        while (d) {
+            ++key_bits;
+            d >>= 1;
+        }
+    }
+    bool overlap = nnz >= (1ull << 22) && key_bits <= 64;
+    for (int k = 0; k < order && overlap; ++k)
+        overlap = d_idx[k] && (reinterpret_cast<uintptr_t>(d_idx[k]) & 15) == 0 && pinned_device_address(d_idx[k]);
+    overlap = overlap && (reinterpret_cast<uintptr_t>(d_val) & 15) == 0 && pinned_device_address(d_val);
+    if (!overlap) {
+        pasta_status st = pasta_coo_create(out, order, dims, nnz, d_idx, d_val, flags, stream);
+        if (st != PASTA_OK) return st;
+        st = pasta_coo_sort_by_mode(*out, mode, stream);
+        if (st != PASTA_OK) {
+            pasta_coo_destroy(*out);
+            *out = nullptr;
+        }
+        return st;
+    }
+    pasta_status st = pasta::make_handle(out, order, dims, nnz, d_idx, d_val, flags | kCreateDeferCopy, stream);
+    if (st != PASTA_OK) return st;
+    pasta_coo_s *X = *out;
+    StoredCopy &c = X->sorted[mode];
+    st = alloc_copy(X, c, true);
+    if (st == PASTA_OK)
+        st = copy_in_and_sort(X, mode, reinterpret_cast<const void *const *>(d_idx), d_val,
+                              static_cast<cudaStream_t>(stream));
+    if (st == PASTA_OK) c.present = true;
+    if (st == PASTA_OK && !(flags & PASTA_CREATE_NO_VALIDATE)) {
+        uint64_t bi = 0, bv = 0;
+        st = validate_coo(X, stream, &bi, &bv);
+        if (st == PASTA_OK && bi) {
+            set_error("%llu index entries are >= their mode size", (unsigned long long)bi);
+            st = PASTA_ERR_INDEX_OOB;
+        } else if (st == PASTA_OK && bv) {
+            set_error("%llu values are NaN or Inf", (unsigned long long)bv);
+            st = PASTA_ERR_NONFINITE;
+        }
+    }
+    if (st != PASTA_OK) {
+        pasta_coo_destroy(X);
+        *out = nullptr;
+    }
+    return st;
 }
 
 pasta_status pasta_coo_destroy(pasta_coo X) {

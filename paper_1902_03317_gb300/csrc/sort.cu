@@ -21,6 +21,7 @@
 // digit in shared memory and written out in runs of equal digit.
 #include <algorithm>
 
+#include "host_copy.cuh"
 #include "pasta_internal.cuh"
 
 namespace pasta {
@@ -319,6 +320,7 @@ struct GatherDst {
     // (shift[k] >= 0, mask[k]); else (shift[k] < 0) gather it through perm.
     int shift[kMaxOrder];
     uint32_t mask[kMaxOrder];
+    int order;
 };
 
 // Writes the sorted copy: indices held whole by the key are decoded from the
@@ -378,6 +380,96 @@ __global__ void k_decode(const uint64_t *keys, uint64_t n, int order, GatherDst 
     }
 }
 
+// ----------------------------------------------------------- two runs ---
+
+// Number of elements of A among the first d of the stable merge of sorted
+// A and B (ties: A first): the first i in [max(0, d - nB), min(d, nA)] whose
+// A[i] is above B[d - i - 1].
+template <typename KA, typename KB>
+__device__ __forceinline__ uint64_t merge_split(KA A, uint64_t nA, KB B, uint64_t nB, uint64_t d) {
+    uint64_t lo = d > nB ? d - nB : 0;
+    uint64_t hi = d < nA ? d : nA;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if (A[mid] <= B[d - mid - 1])
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo;
+}
+
+// Dynamic shared memory of k_merge_decode: a tile of input pairs, then the
+// tile merged.
+constexpr size_t kMergeSmem = 2 * (size_t)kTile * (sizeof(uint64_t) + sizeof(uint32_t));
+
+// Stable merge of the sorted runs (kA, vA) and (kB, vB) (ties: A first, A
+// holding the earlier entries) written as the sorted copy: position p gets
+// the indices decoded from its key and the value whose bits are its payload.
+// Block b writes positions [b kTile, (b + 1) kTile): it finds where that
+// range starts and ends in A and B, loads both pieces into shared memory,
+// each thread merges kItems outputs from its own split point, and the block
+// writes the tile out in order.
+__global__ void __launch_bounds__(kThreads) k_merge_decode(const uint64_t *kA, const uint32_t *vA, uint64_t nA,
+                                                           const uint64_t *kB, const uint32_t *vB, uint64_t nB,
+                                                           GatherDst dst) {
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    uint64_t *ik = reinterpret_cast<uint64_t *>(sm_raw);
+    uint32_t *iv = reinterpret_cast<uint32_t *>(sm_raw + (size_t)kTile * sizeof(uint64_t));
+    uint64_t *ok = reinterpret_cast<uint64_t *>(sm_raw + (size_t)kTile * (sizeof(uint64_t) + sizeof(uint32_t)));
+    uint32_t *ov = reinterpret_cast<uint32_t *>(sm_raw + (size_t)kTile * (2 * sizeof(uint64_t) + sizeof(uint32_t)));
+    __shared__ uint64_t split[2];
+    const int t = threadIdx.x;
+    const uint64_t n = nA + nB;
+    const uint64_t d0 = (uint64_t)blockIdx.x * kTile;
+    const uint64_t d1 = min(n, d0 + kTile);
+    if (t < 2) split[t] = merge_split(kA, nA, kB, nB, t == 0 ? d0 : d1);
+    __syncthreads();
+    const uint64_t i0 = split[0], i1 = split[1];
+    const int lenA = (int)(i1 - i0);
+    const int len = (int)(d1 - d0);
+    const int lenB = len - lenA;
+    const uint64_t j0 = d0 - i0;
+    for (int q = t; q < lenA; q += kThreads) {
+        ik[q] = kA[i0 + q];
+        iv[q] = vA[i0 + q];
+    }
+    for (int q = t; q < lenB; q += kThreads) {
+        ik[lenA + q] = kB[j0 + q];
+        iv[lenA + q] = vB[j0 + q];
+    }
+    __syncthreads();
+    const int o0 = t * kItems;
+    if (o0 < len) {
+        const uint64_t *A = ik;
+        const uint64_t *B = ik + lenA;
+        int i = (int)merge_split(A, (uint64_t)lenA, B, (uint64_t)lenB, (uint64_t)o0);
+        int j = o0 - i;
+        const int o1 = min(len, o0 + kItems);
+        for (int o = o0; o < o1; ++o) {
+            const bool takeA = j >= lenB || (i < lenA && A[i] <= B[j]);
+            if (takeA) {
+                ok[o] = A[i];
+                ov[o] = iv[i];
+                ++i;
+            } else {
+                ok[o] = B[j];
+                ov[o] = iv[lenA + j];
+                ++j;
+            }
+        }
+    }
+    __syncthreads();
+    for (int q = t; q < len; q += kThreads) {
+        const uint64_t key = ok[q];
+        const uint64_t p = d0 + q;
+#pragma unroll
+        for (int k = 0; k < kMaxOrder; ++k)
+            if (k < dst.order) dst.idx[k][p] = (uint32_t)(key >> dst.shift[k]) & dst.mask[k];
+        dst.val[p] = __uint_as_float(ov[q]);
+    }
+}
+
 int bits_for(uint64_t dim) {
     int b = 0;
     while (b < 64 && (dim - 1) >> b) ++b;
@@ -430,6 +522,7 @@ GatherDst decode_spec(const pasta_coo_s *X, const KeySpec &ks, const StoredCopy 
         }
     }
     gd.val = dst.val;
+    gd.order = X->order;
     return gd;
 }
 
@@ -441,20 +534,30 @@ GatherDst decode_spec(const pasta_coo_s *X, const KeySpec &ks, const StoredCopy 
 // sorted keys inside the handle's scratch (valid until its next use).
 // The passes of the radix sort over keys and payloads that `make` writes
 // into the scratch (see radix_sort).
+// Scratch bytes of one radix sort of n pairs: two key buffers, the spare
+// payload buffer, the histograms.
+size_t radix_scratch_bytes(uint64_t n) {
+    const uint64_t ntiles = (n + kTile - 1) / kTile;
+    const size_t hist_n = (size_t)kMaxBins * ntiles + kMaxBins;
+    const size_t keys_b = (2 * n * sizeof(uint64_t) + 255) & ~(size_t)255;
+    const size_t tmpv_b = (n * sizeof(uint32_t) + 255) & ~(size_t)255;
+    return keys_b + tmpv_b + ((hist_n * sizeof(uint32_t) + 255) & ~(size_t)255);
+}
+
 template <typename Make>
 pasta_status radix_core(pasta_coo_s *X, uint64_t n, int low, int used, Make make, uint32_t *payload_out,
-                        const uint64_t **keys_sorted, cudaStream_t s) {
+                        const uint64_t **keys_sorted, cudaStream_t s, void *scratch_at = nullptr) {
     // digits of at most 9 bits, balanced over the fewest passes: 57 bits take
     // 7 passes (one of 9 bits), 64 take 8 of 8
     const int bits = used - low;
     const int passes = (bits + 8) / 9;
     const uint32_t ntiles = (uint32_t)((n + kTile - 1) / kTile);
-    // scratch: two key buffers, the spare payload buffer, the histograms
-    const size_t hist_n = (size_t)kMaxBins * ntiles + kMaxBins;
+    // scratch (radix_scratch_bytes): the handle's, or the region given
     const size_t keys_b = (2 * n * sizeof(uint64_t) + 255) & ~(size_t)255;
     const size_t tmpv_b = (n * sizeof(uint32_t) + 255) & ~(size_t)255;
-    void *base = nullptr;
-    pasta_status st = handle_scratch(X, keys_b + tmpv_b + hist_n * sizeof(uint32_t), &base);
+    void *base = scratch_at;
+    pasta_status st = PASTA_OK;
+    if (!base) st = handle_scratch(X, radix_scratch_bytes(n), &base);
     if (st != PASTA_OK) return st;
     uint64_t *keys = reinterpret_cast<uint64_t *>(base);
     uint32_t *tmpv = reinterpret_cast<uint32_t *>(static_cast<char *>(base) + keys_b);
@@ -495,11 +598,24 @@ pasta_status radix_core(pasta_coo_s *X, uint64_t n, int low, int used, Make make
     return PASTA_OK;
 }
 
+pasta_status radix_sort_view(pasta_coo_s *X, const CooView &src, const KeySpec &ks, int low, int used,
+                             bool payload_val, uint32_t *payload_out, const uint64_t **keys_sorted,
+                             cudaStream_t s, void *scratch_at);
+
 pasta_status radix_sort(pasta_coo_s *X, const StoredCopy &srcc, const KeySpec &ks, int low, int used,
                         bool payload_val, uint32_t *payload_out, const uint64_t **keys_sorted,
                         cudaStream_t s) {
-    const uint64_t n = X->nnz;
-    const CooView src = view_of(X, srcc);
+    return radix_sort_view(X, view_of(X, srcc), ks, low, used, payload_val, payload_out, keys_sorted, s,
+                           nullptr);
+}
+
+// radix_sort over the entries of a view (src.nnz of them; each array 16-byte
+// aligned and readable 16 bytes past its end), with the scratch given
+// (nullptr: the handle's).
+pasta_status radix_sort_view(pasta_coo_s *X, const CooView &src, const KeySpec &ks, int low, int used,
+                             bool payload_val, uint32_t *payload_out, const uint64_t **keys_sorted,
+                             cudaStream_t s, void *scratch_at) {
+    const uint64_t n = src.nnz;
     const int gblocks = (int)std::min<uint64_t>((n + 255) / 256, (uint64_t)X->num_sms * 16);
     return radix_core(
         X, n, low, used,
@@ -508,7 +624,7 @@ pasta_status radix_sort(pasta_coo_s *X, const StoredCopy &srcc, const KeySpec &k
             PASTA_CUDA(cudaGetLastError());
             return PASTA_OK;
         },
-        payload_out, keys_sorted, s);
+        payload_out, keys_sorted, s, scratch_at);
 }
 
 bool key_holds_all(const GatherDst &gd, int order) {
@@ -570,6 +686,94 @@ pasta_status sort_copy(pasta_coo_s *X, int mode, cudaStream_t s) {
     cudaError_t le = cudaGetLastError();
     if (le != cudaSuccess) return cuda_fail(le, "sort kernels");
     return PASTA_OK;
+}
+
+bool sort_key_holds_all(const pasta_coo_s *X, int mode) {
+    int used = 0;
+    const KeySpec ks = key_spec(X, mode, &used);
+    StoredCopy none{};
+    return key_holds_all(decode_spec(X, ks, none), X->order);
+}
+
+pasta_status copy_in_and_sort(pasta_coo_s *X, int mode, const void *const *h_idx, const void *h_val, cudaStream_t s) {
+    const uint64_t n = X->nnz;
+    const uint64_t nA = (n / 2) & ~(uint64_t)1023;  // 16-byte aligned split of every array
+    const uint64_t nB = n - nA;
+    StoredCopy &dst = X->sorted[mode];
+    dst.perm_ready = false;
+    int used = 0;
+    const KeySpec ks = key_spec(X, mode, &used);
+    const GatherDst gd = decode_spec(X, ks, dst);
+    if (!key_holds_all(gd, X->order) || nA == 0) {
+        set_error("copy_in_and_sort needs a key that holds every index and at least 1024 entries per half");
+        return PASTA_ERR_UNSUPPORTED;
+    }
+    // scratch: a radix region per half, then each half's sorted payload
+    const size_t rA = radix_scratch_bytes(nA), rB = radix_scratch_bytes(nB);
+    const size_t pA = (nA * sizeof(uint32_t) + 255) & ~(size_t)255;
+    const size_t pB = (nB * sizeof(uint32_t) + 255) & ~(size_t)255;
+    void *base = nullptr;
+    pasta_status st = handle_scratch(X, rA + rB + pA + pB, &base);
+    if (st != PASTA_OK) return st;
+    char *b = static_cast<char *>(base);
+    void *scrA = b, *scrB = b + rA;
+    uint32_t *payA = reinterpret_cast<uint32_t *>(b + rA + rB);
+    uint32_t *payB = reinterpret_cast<uint32_t *>(b + rA + rB + pA);
+
+    // the second half's copy runs on a high-priority stream of its own, so
+    // its (small) grid is scheduled while the first half's sort fills the GPU
+    int lo_pri = 0, hi_pri = 0;
+    PASTA_CUDA(cudaDeviceGetStreamPriorityRange(&lo_pri, &hi_pri));
+    cudaStream_t sc = nullptr;
+    cudaEvent_t evA = nullptr, evB = nullptr;
+    PASTA_CUDA(cudaStreamCreateWithPriority(&sc, cudaStreamNonBlocking, hi_pri));
+    cudaError_t e = cudaEventCreateWithFlags(&evA, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evB, cudaEventDisableTiming);
+    const int order = X->order;
+    // first half on the caller's stream, the second half on sc after it
+    for (int k = 0; k < order && e == cudaSuccess; ++k)
+        e = copy_bytes(X->orig.idx[k], h_idx[k], nA * 4, X->num_sms, s);
+    if (e == cudaSuccess) e = copy_bytes(X->orig.val, h_val, nA * 4, X->num_sms, s);
+    if (e == cudaSuccess) e = cudaEventRecord(evA, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc, evA, 0);
+    for (int k = 0; k < order && e == cudaSuccess; ++k)
+        e = copy_bytes(X->orig.idx[k] + nA, static_cast<const uint32_t *>(h_idx[k]) + nA, nB * 4, X->num_sms, sc);
+    if (e == cudaSuccess)
+        e = copy_bytes(X->orig.val + nA, static_cast<const float *>(h_val) + nA, nB * 4, X->num_sms, sc);
+    if (e == cudaSuccess) e = cudaEventRecord(evB, sc);
+    if (e != cudaSuccess) st = cuda_fail(e, "copy-in of the halves");
+    // the first half sorts while the second half arrives
+    const uint64_t *keysA = nullptr, *keysB = nullptr;
+    if (st == PASTA_OK) {
+        CooView va = view_of(X, X->orig);
+        va.nnz = nA;
+        st = radix_sort_view(X, va, ks, 0, used, true, payA, &keysA, s, scrA);
+    }
+    if (st == PASTA_OK) {
+        e = cudaStreamWaitEvent(s, evB, 0);
+        if (e != cudaSuccess) st = cuda_fail(e, "wait for the second half");
+    }
+    if (st == PASTA_OK) {
+        CooView vb = view_of(X, X->orig);
+        for (int k = 0; k < order; ++k) vb.idx[k] += nA;
+        vb.val += nA;
+        vb.nnz = nB;
+        st = radix_sort_view(X, vb, ks, 0, used, true, payB, &keysB, s, scrB);
+    }
+    if (st == PASTA_OK) {
+        e = cudaFuncSetAttribute(k_merge_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMergeSmem);
+        if (e == cudaSuccess) {
+            const unsigned blocks = (unsigned)((n + kTile - 1) / kTile);
+            k_merge_decode<<<blocks, kThreads, kMergeSmem, s>>>(keysA, payA, nA, keysB, payB, nB, gd);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) st = cuda_fail(e, "merge of the sorted halves");
+    }
+    // stream and events are released once the work queued on them is done
+    if (evA) cudaEventDestroy(evA);
+    if (evB) cudaEventDestroy(evB);
+    cudaStreamDestroy(sc);
+    return st;
 }
 
 pasta_status radix_sort_keys(pasta_coo_s *X, uint64_t n, int used, MakeKeysFn make, void *ctx,

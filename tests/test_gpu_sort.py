@@ -186,8 +186,62 @@ def test_memcpy_every_direction(nbytes):
     G.pasta.copy_(d3, h)  # pageable source
     torch.cuda.synchronize()
     assert torch.equal(d2.cpu(), h) and torch.equal(d3.cpu(), h)
-    # an offset view (4-byte aligned, not 16): the copy-engine path
+    # an offset view (4-byte aligned, not 16): the copy-engine path; a
+    # 16-byte aligned interior view of the pinned block: the kernel path
     if n > 2:
         G.pasta.copy_(d[1:], hp[1:])
         torch.cuda.synchronize()
         assert torch.equal(d.cpu(), h)
+    if n > 4:
+        d.zero_()
+        G.pasta.copy_(d[4:], hp[4:])
+        back.zero_()
+        G.pasta.copy_(back[4:], d[4:])
+        torch.cuda.synchronize()
+        assert torch.equal(d[4:].cpu(), h[4:]) and torch.equal(back[4:], h[4:])
+
+
+@pytest.mark.parametrize("name,nnz,dims,mode", [
+    ("zipf3d", 5_000_003, (200_000, 100_000, 40_000), 0),
+    ("zipf4d", 4_500_001, (50_000, 50_000, 5_000, 1_000), 2),   # duplicates kept, odd halves
+])
+def test_create_sorted_overlapped_matches_oracle(name, nnz, dims, mode):
+    """pasta_coo_create_sorted from pinned host arrays (>= 2^22 entries: the
+    first half sorted while the second is copied in, then merged) gives the
+    oracle's permutation and sorted copy bit for bit, and the creation-order
+    copy unchanged; the other modes sort from it as usual."""
+    Xh = G.generate(G.small(name, nnz, dims))
+    idx, val = G.host(Xh)
+    idx_h = [i.contiguous().pin_memory() for i in Xh.idx]
+    val_h = Xh.val.contiguous().pin_memory()
+    X = G.pasta.CooTensor(Xh.dims, idx_h, val_h, device=G.DEV, sort_mode=mode)
+    sidx, sval, perm = X.copy_out(mode)
+    perm = perm.cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(perm, oracle.sort_perm(idx, mode))
+    for k in range(len(dims)):
+        np.testing.assert_array_equal(sidx[k].cpu().numpy().astype(np.uint32), idx[k][perm])
+    np.testing.assert_array_equal(sval.cpu().numpy(), val[perm].astype(np.float32))
+    oidx, oval, _ = X.copy_out(-1)
+    for k in range(len(dims)):
+        assert torch.equal(oidx[k].cpu(), Xh.idx[k])
+    assert torch.equal(oval.cpu(), Xh.val)
+    nxt = (mode + len(dims) - 1) % len(dims)
+    X.sort_by_mode(nxt)
+    _, _, p2 = X.copy_out(nxt)
+    np.testing.assert_array_equal(p2.cpu().numpy().astype(np.int64), oracle.sort_perm(idx, nxt))
+    X.close()
+
+
+def test_create_sorted_fallbacks_and_errors():
+    """Below 2^22 entries, or from device memory, create_sorted runs create
+    and sort; a mode outside [0, order) is refused."""
+    Xh = G.generate(G.small("zipf3d", 30_001, (3_000, 2_000, 1_000)))
+    idx, _ = G.host(Xh)
+    for X in (G.pasta.CooTensor(Xh.dims, [i.pin_memory() for i in Xh.idx], Xh.val.pin_memory(),
+                                device=G.DEV, sort_mode=1),
+              G.pasta.CooTensor(Xh.dims, [i.to(G.DEV) for i in Xh.idx], Xh.val.to(G.DEV), sort_mode=1)):
+        _, _, perm = X.copy_out(1)
+        np.testing.assert_array_equal(perm.cpu().numpy().astype(np.int64), oracle.sort_perm(idx, 1))
+        X.close()
+    with pytest.raises(G.pasta.PastaError):
+        G.pasta.CooTensor(Xh.dims, [i.to(G.DEV) for i in Xh.idx], Xh.val.to(G.DEV), sort_mode=3)
