@@ -204,6 +204,7 @@ def test_memcpy_every_direction(nbytes):
 @pytest.mark.parametrize("name,nnz,dims,mode", [
     ("zipf3d", 5_000_003, (200_000, 100_000, 40_000), 0),
     ("zipf4d", 4_500_001, (50_000, 50_000, 5_000, 1_000), 2),   # duplicates kept, odd halves
+    ("zipf3d", 17_000_001, (400_000, 200_000, 80_000), 1),      # larger halves, another mode
 ])
 def test_create_sorted_overlapped_matches_oracle(name, nnz, dims, mode):
     """pasta_coo_create_sorted from pinned host arrays (>= 2^22 entries: the
