@@ -406,26 +406,35 @@ constexpr size_t kMergeSmem = 2 * (size_t)kTile * (sizeof(uint64_t) + sizeof(uin
 // Stable merge of the sorted runs (kA, vA) and (kB, vB) (ties: A first, A
 // holding the earlier entries) written as the sorted copy: position p gets
 // the indices decoded from its key and the value whose bits are its payload.
-// Block b writes positions [b kTile, (b + 1) kTile): it finds where that
-// range starts and ends in A and B, loads both pieces into shared memory,
-// each thread merges kItems outputs from its own split point, and the block
-// writes the tile out in order.
+// Block b writes positions [b kTile, (b + 1) kTile): split[b] and
+// split[b + 1] (k_merge_splits) say where that range starts and ends in A and
+// B; it loads both pieces into shared memory, each thread merges kItems
+// outputs from its own split point, and the block writes the tile out in
+// order.
+// split[b] = merge_split(A, B, min(b kTile, nA + nB)) for b in [0, nblocks]:
+// where each merge block's output range starts in A (one thread per block
+// boundary, so the searches' dependent loads overlap across threads).
+__global__ void k_merge_splits(const uint64_t *kA, uint64_t nA, const uint64_t *kB, uint64_t nB, uint64_t nblocks,
+                               uint64_t *split) {
+    const uint64_t b = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b > nblocks) return;
+    const uint64_t d = min(b * (uint64_t)kTile, nA + nB);
+    split[b] = merge_split(kA, nA, kB, nB, d);
+}
+
 __global__ void __launch_bounds__(kThreads) k_merge_decode(const uint64_t *kA, const uint32_t *vA, uint64_t nA,
                                                            const uint64_t *kB, const uint32_t *vB, uint64_t nB,
-                                                           GatherDst dst) {
+                                                           const uint64_t *split, GatherDst dst) {
     extern __shared__ __align__(16) unsigned char sm_raw[];
     uint64_t *ik = reinterpret_cast<uint64_t *>(sm_raw);
     uint32_t *iv = reinterpret_cast<uint32_t *>(sm_raw + (size_t)kTile * sizeof(uint64_t));
     uint64_t *ok = reinterpret_cast<uint64_t *>(sm_raw + (size_t)kTile * (sizeof(uint64_t) + sizeof(uint32_t)));
     uint32_t *ov = reinterpret_cast<uint32_t *>(sm_raw + (size_t)kTile * (2 * sizeof(uint64_t) + sizeof(uint32_t)));
-    __shared__ uint64_t split[2];
     const int t = threadIdx.x;
     const uint64_t n = nA + nB;
     const uint64_t d0 = (uint64_t)blockIdx.x * kTile;
     const uint64_t d1 = min(n, d0 + kTile);
-    if (t < 2) split[t] = merge_split(kA, nA, kB, nB, t == 0 ? d0 : d1);
-    __syncthreads();
-    const uint64_t i0 = split[0], i1 = split[1];
+    const uint64_t i0 = split[blockIdx.x], i1 = split[blockIdx.x + 1];
     const int lenA = (int)(i1 - i0);
     const int len = (int)(d1 - d0);
     const int lenB = len - lenA;
@@ -712,13 +721,16 @@ pasta_status copy_in_and_sort(pasta_coo_s *X, int mode, const void *const *h_idx
     const size_t rA = radix_scratch_bytes(nA), rB = radix_scratch_bytes(nB);
     const size_t pA = (nA * sizeof(uint32_t) + 255) & ~(size_t)255;
     const size_t pB = (nB * sizeof(uint32_t) + 255) & ~(size_t)255;
+    const uint64_t mblocks = (n + kTile - 1) / kTile;
+    const size_t sp = ((mblocks + 1) * sizeof(uint64_t) + 255) & ~(size_t)255;
     void *base = nullptr;
-    pasta_status st = handle_scratch(X, rA + rB + pA + pB, &base);
+    pasta_status st = handle_scratch(X, rA + rB + pA + pB + sp, &base);
     if (st != PASTA_OK) return st;
     char *b = static_cast<char *>(base);
     void *scrA = b, *scrB = b + rA;
     uint32_t *payA = reinterpret_cast<uint32_t *>(b + rA + rB);
     uint32_t *payB = reinterpret_cast<uint32_t *>(b + rA + rB + pA);
+    uint64_t *splits = reinterpret_cast<uint64_t *>(b + rA + rB + pA + pB);
 
     // the second half's copy runs on a high-priority stream of its own, so
     // its (small) grid is scheduled while the first half's sort fills the GPU
@@ -763,8 +775,9 @@ pasta_status copy_in_and_sort(pasta_coo_s *X, int mode, const void *const *h_idx
     if (st == PASTA_OK) {
         e = cudaFuncSetAttribute(k_merge_decode, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMergeSmem);
         if (e == cudaSuccess) {
-            const unsigned blocks = (unsigned)((n + kTile - 1) / kTile);
-            k_merge_decode<<<blocks, kThreads, kMergeSmem, s>>>(keysA, payA, nA, keysB, payB, nB, gd);
+            k_merge_splits<<<(unsigned)((mblocks + 1 + 255) / 256), 256, 0, s>>>(keysA, nA, keysB, nB, mblocks, splits);
+            k_merge_decode<<<(unsigned)mblocks, kThreads, kMergeSmem, s>>>(keysA, payA, nA, keysB, payB, nB, splits,
+                                                                           gd);
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) st = cuda_fail(e, "merge of the sorted halves");
