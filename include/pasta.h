@@ -124,12 +124,13 @@ pasta_status pasta_coo_create(pasta_coo *out, int order, const uint64_t *dims, u
  * pasta_coo_create_sorted -- pasta_coo_create followed by
  * pasta_coo_sort_by_mode(mode), with the same arguments, result and errors,
  * but overlapped: for at least 2^22 entries in pinned host memory (every
- * array 16-byte aligned) whose sort key holds every index, the first half of
- * the entries is copied in and sorted while the second half is copied (on a
- * high-priority stream of the library's own, joined back to `stream`), then
- * the second half is sorted and the two sorted halves are merged (stable,
- * ties to the first half: the order one sort gives).  Otherwise it runs the
- * two calls.  The sort's scratch grows to about 24 bytes per entry.
+ * array 16-byte aligned) whose sort key holds every index, the entries are
+ * cut into parts (4 from 2^24 entries on, else 2); each part is sorted once
+ * it has been copied in while the later parts are still being copied (on a
+ * high-priority stream of the library's own, joined back to `stream`), and
+ * the sorted parts are merged (stable, ties to the earlier part: the order
+ * one sort gives).  Otherwise it runs the two calls.  The sort's scratch
+ * grows to about 24 (2 parts) or 36 (4 parts) bytes per entry.
  * PASTA_ERR_INVALID_ARG also for mode outside [0, order).
  */
 pasta_status pasta_coo_create_sorted(pasta_coo *out, int order, const uint64_t *dims, uint64_t nnz,

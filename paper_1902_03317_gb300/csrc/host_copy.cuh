@@ -22,12 +22,13 @@ const void *pinned_device_address(const void *p);
 bool sort_key_holds_all(const ::pasta_coo_s *X, int mode);
 
 // The creation-order copy filled from pinned host arrays and the mode's sorted
-// copy built, overlapped: the first half of the entries is copied and sorted
-// while the second half is copied (on a high-priority stream of its own),
-// then the second half is sorted and the two sorted halves are merged into the
-// sorted copy (stable, the first half first on ties: the same order as one
-// sort).  Needs a key that holds every index and nnz >= 2048; the sorted
-// copy must be allocated.  Defined in sort.cu.
+// copy built, overlapped: the entries are cut into K parts (4 from 2^24
+// entries on, else 2); each part is sorted as soon as it has been copied
+// while the later parts are still being copied (on a high-priority stream of
+// their own), and the sorted parts are merged into the sorted copy (stable,
+// earlier parts first on ties: the same order as one sort).  Needs a key that
+// holds every index and at least 1024 entries per part; the sorted copy must
+// be allocated.  Defined in sort.cu.
 pasta_status copy_in_and_sort(::pasta_coo_s *X, int mode, const void *const *h_idx, const void *h_val,
                               cudaStream_t s);
 
