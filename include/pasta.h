@@ -296,7 +296,8 @@ pasta_status pasta_cp_loss_bwd(pasta_coo X, const void *const *d_U, pasta_dtype 
  * (cudaGetSymbolAddress).  The first call on a device may load the library's
  * device code, which allocates, and so may the first call after
  * cudaDeviceReset (the array may then sit at a new address, which the lookup
- * finds); later calls allocate nothing.
+ * finds); later calls allocate nothing.  So make the first call on each
+ * device (and the first after a reset) before any stream capture begins.
  */
 #define PASTA_NOALLOC_MAX_PARTIALS 4096
 
